@@ -1,0 +1,184 @@
+/*
+ * amr.h — C ABI of libamr: octree-AMR volume ray casting on one GB300 GPU.
+ *
+ * The operation is the ray-casting pass of Sec. 2.2 ("The volume ray casting
+ * technique"): one ray per pixel; each leaf cell the ray crosses contributes its
+ * value times the length between the ray's entry and exit points on the cell
+ * faces; contributions are added in any order.  The camera fixes the deepest
+ * octree level read, so cells at that level act as leaves (Sec. 2, first
+ * paragraph).  Besides the column integral the library computes a
+ * density-weighted mean of the line-of-sight velocity and the maximum along the
+ * ray (maximum-intensity projection, Sec. 2.1 last sentence).
+ *
+ * Geometry.  The box is the unit cube [0,1)^3.  The root oct has level 1 and
+ * its 8 cells have edge 1/2; a cell of level l has edge 2^-l, l <= 22 (Sec. 1:
+ * the Milky-Way run is refined to level 22).  Cell c of an oct sits at offset
+ * (c&1, c>>1&1, c>>2&1); cells are half-open.  Cameras are orthographic: pixel
+ * (i, j) is centred at
+ *     centre + ((i+0.5)/nx - 0.5) fov[0] u + ((j+0.5)/ny - 0.5) fov[1] v
+ * (IEEE double, in that order, no contraction) and its ray is the whole line
+ * through that point along +w.  Map row j = 0 is the -v edge; i runs along +u.
+ * The ray is quantised (origin round-half-even(x 2^36) per axis, direction
+ * round-half-even(w / max|w_a| 2^23)) and every traversal decision is an exact
+ * integer comparison on that line, so the visited-leaf counts are exact.
+ *
+ * Conventions for every function:
+ *   - return AMR_OK (0) or a negative amr_status; never abort the process;
+ *   - on error, amr_last_error() returns a message for the calling thread;
+ *   - the caller owns every pointer it passes; the library copies what it keeps;
+ *   - a context is not thread-safe, except amr_submit / amr_wait / amr_stats,
+ *     which may be called from any thread.
+ */
+#ifndef AMR_H
+#define AMR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amr_ctx amr_ctx;   /* opaque; owns device memory and streams */
+typedef int32_t amr_status;
+
+enum {
+  AMR_OK = 0,
+  AMR_E_INVALID = -1,    /* bad argument or camera */
+  AMR_E_BADTREE = -2,    /* tree arrays fail validation (the oct index is in the message) */
+  AMR_E_OOM = -3,        /* device or host allocation failed, or over the memory limit */
+  AMR_E_CUDA = -4,       /* a CUDA call failed (its error text is in the message) */
+  AMR_E_TIMEOUT = -5,    /* amr_wait ran out of time */
+  AMR_E_BUSY = -6,       /* the request queue is full */
+  AMR_E_CANCELLED = -7   /* the request was cancelled or the context is shutting down */
+};
+
+enum { AMR_F32 = 0, AMR_F64 = 1 };
+enum { AMR_MODE_COLUMN = 0, AMR_MODE_WMEAN = 1, AMR_MODE_MAX = 2 };
+enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32_KAHAN = 1, AMR_PREC_FP32_PLAIN = 2 };
+#define AMR_LEVEL_AUTO (-1)   /* deepest level whose cell edge is at least one pixel */
+
+/*
+ * A camera (copied at the call).
+ *   centre, u, v, w : box units; u, v, w orthonormal to 1e-9; w is the ray direction.
+ *   fov             : extent of the map along u and v (orthographic).
+ *   nx, ny          : map size in pixels (nx*ny < 2^31).
+ *   max_level       : > 0: read levels <= min(max_level, tree depth);
+ *                     AMR_LEVEL_AUTO: the deepest level l with 2^-l >= fov[a]/n_a
+ *                     on both axes (cells at least one pixel wide, Sec. 2),
+ *                     clamped to [1, tree depth].
+ *   mode            : AMR_MODE_COLUMN  sum rho*len over crossed leaves
+ *                     AMR_MODE_WMEAN   sum rho*(v.w)*len / sum rho*len (0 if empty)
+ *                     AMR_MODE_MAX     max rho over crossed leaves (0 if empty)
+ *   precision       : AMR_PREC_FP64 (plain double sums, double map);
+ *                     AMR_PREC_FP32_KAHAN (float chords, compensated float sums,
+ *                     float map); AMR_PREC_FP32_PLAIN (uncompensated float sums).
+ *   field_value     : field used as rho in column and max modes.
+ *   field_weight    : field used as rho in wmean mode.
+ *   field_vel[3]    : velocity component fields for wmean mode.
+ * Every pixel centre must lie in [-1, 2]^3 (it keeps every exact product below
+ * 2^62); otherwise AMR_E_INVALID.
+ */
+typedef struct {
+  double centre[3], u[3], v[3], w[3];
+  double fov[2];
+  int32_t nx, ny, max_level, mode, precision;
+  int32_t field_value, field_weight;
+  int32_t field_vel[3];
+} amr_camera;
+
+/* Launch configuration; chosen by amr_autotune or set by hand. */
+typedef struct {
+  int32_t tile_w, tile_h;     /* pixels per warp work item: tile_w*tile_h == 32 */
+  int32_t block_threads;      /* threads per block: 64..1024, multiple of 32 */
+  int32_t blocks_per_sm;      /* persistent grid = SMs x this (0 = occupancy limit) */
+  int32_t tiles_per_grab;     /* work items a warp takes from the queue at once (>= 1) */
+  int32_t use_graph;          /* replay batches through a captured CUDA graph */
+} amr_options;
+
+/* Create a context on CUDA device `device` (allocates the work queue and a stream). */
+amr_status amr_create(amr_ctx** out, int device);
+/* Destroy a context: waits for its work, frees all device memory it owns. */
+amr_status amr_destroy(amr_ctx* ctx);
+
+/*
+ * Load (replace) the octree.  Host arrays, n_oct octs:
+ *   level[n_oct]        uint8, root = oct 0 at level 1, levels <= 22
+ *   coord[n_oct][3]     int32 corner of the oct's cell 0 in level-l cell units (even)
+ *   child[n_oct][8]     int32 oct refining cell c, or -1 (leaf)
+ *   fields[n_fields]    each [n_oct][8] of float (AMR_F32) or double (AMR_F64)
+ * Validation (AMR_E_BADTREE, oct index in the message): root at index 0, level 1,
+ * coord 0; child level = parent level + 1; child coord = 2 (parent coord + offset
+ * of c); every non-root oct referenced exactly once; coordinates in range.
+ * The arrays are renumbered breadth-first (siblings contiguous) into 8-byte oct
+ * records {first child, refinement mask} plus one array per field, and copied to
+ * device memory owned by the context; the caller may free its arrays on return.
+ * Synchronous.
+ */
+amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, const int32_t* coord,
+                           const int32_t* child, int32_t n_fields, const void* const* fields,
+                           int32_t field_dtype);
+
+/*
+ * Render one camera.  map_out: nx*ny values, double for AMR_PREC_FP64 and float
+ * otherwise, row-major [ny][nx].  count_out (nullable): nx*ny int32 visited-leaf
+ * counts.  out_on_device != 0: both are device pointers and the call returns once
+ * the work is enqueued on `cuda_stream` (a cudaStream_t; NULL = the context's own
+ * stream); out_on_device == 0: host pointers, and the call returns when the
+ * results are in them.
+ */
+amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* count_out,
+                      int out_on_device, void* cuda_stream);
+
+/*
+ * Render n cameras (uneven sizes, levels, modes) in one persistent launch per
+ * precision, fed by a device work queue of ray tiles (Sec. 3.2: a master hands
+ * out work to whichever worker is free).  maps[i] / counts[i] as in amr_render;
+ * counts may be NULL, and so may any counts[i].
+ */
+amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
+                            int32_t* const* counts, int out_on_device, void* cuda_stream);
+
+/* Validate a camera against the loaded tree; *level_out (nullable) receives the
+ * level cut it renders at. */
+amr_status amr_camera_check(amr_ctx* ctx, const amr_camera* cam, int32_t* level_out);
+
+amr_status amr_set_options(amr_ctx* ctx, const amr_options* opt);
+amr_status amr_get_options(amr_ctx* ctx, amr_options* opt);
+
+/*
+ * Time candidate launch configurations on this batch (each run `reps` times,
+ * device results discarded) and keep the fastest in the context.  *best (nullable)
+ * receives it; ms_out (nullable) its time.
+ */
+amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t reps,
+                        amr_options* best, double* ms_out);
+
+/*
+ * Serving (Sec. 1: iterative interactive zoom).  amr_submit queues a request and
+ * returns at once with a ticket; a server thread admits queued requests while
+ * free slots and the map-memory budget allow, renders the admitted set as one
+ * batch on one of several streams (so a batch admitted while others run overlaps
+ * them on the device), and copies each result into the caller's HOST buffers
+ * `map` / `counts` (nullable), which must stay valid until amr_wait returns for
+ * the ticket.  amr_wait blocks until the ticket completes or timeout_us elapses
+ * (AMR_E_TIMEOUT; the request stays queued; timeout_us < 0 waits forever).
+ * amr_server_config sets the slot count (concurrent batches, 1..8) and the map
+ * memory budget in bytes (0 = 1 GiB); call it before the first amr_submit.
+ */
+amr_status amr_server_config(amr_ctx* ctx, int32_t slots, int64_t map_budget_bytes, int32_t max_batch);
+amr_status amr_submit(amr_ctx* ctx, const amr_camera* cam, void* map, int32_t* counts, uint64_t* ticket);
+amr_status amr_wait(amr_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket);
+
+/* JSON counters: renders, rays, segments, tree bytes, options, server latency. */
+amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len);
+
+/* Device memory the loaded tree occupies, its oct count and depth. */
+amr_status amr_tree_info(amr_ctx* ctx, int64_t* n_oct, int32_t* depth, int64_t* device_bytes);
+
+/* Message of the calling thread's last error (static storage; ctx may be NULL). */
+const char* amr_last_error(amr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -97,7 +97,7 @@ def build_amr(force: bool = False) -> Path:
     if force or _stale(AMR_LIB, objs):
         tmp = AMR_LIB.with_suffix(".so.tmp")
         _run([_nvcc(), ARCH, "-shared", "-o", str(tmp)] + [str(o) for o in objs] +
-             ["-lcudart", "-lpthread"])
+             ["-cudart=static", "-lpthread"])
         tmp.replace(AMR_LIB)
     return AMR_LIB
 

@@ -1,0 +1,1011 @@
+// Host side of the libamr C ABI: tree validation and linearisation, camera
+// canonicalisation, persistent batch launches, autotuning and the request
+// server.  Every path that computes ray results goes through the CUDA kernels
+// in amr_kernels.cu; there is no host fallback.
+#include "amr.h"
+#include "amr_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+using amr::CamDev;
+using amr::QueueBlock;
+
+namespace {
+
+thread_local std::string g_err;
+
+amr_status fail(amr_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(AMR_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DeviceTree {
+  uint2* rec = nullptr;
+  std::vector<void*> fields;
+  int64_t n_oct = 0;
+  int depth = 0;
+  bool f64 = false;
+  int64_t bytes = 0;
+};
+
+// One launch's scratch: camera table, tile prefix sums, queue blocks, and the
+// pinned host mirrors they are uploaded from / read back into.
+struct LaunchSlot {
+  int cap = 0;  // cameras
+  CamDev* h_cams = nullptr;
+  int32_t* h_tiles = nullptr;  // kMaxPrecisions x (cap + 1)
+  QueueBlock* h_q = nullptr;   // kMaxPrecisions
+  CamDev* d_cams = nullptr;
+  int32_t* d_tiles = nullptr;
+  QueueBlock* d_q = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
+  bool pending = false;  // a launch whose results are not yet harvested
+  int n_groups = 0;
+};
+
+struct Request {
+  amr_camera cam;
+  void* map = nullptr;
+  int32_t* counts = nullptr;
+  int64_t bytes = 0;
+  amr_status status = AMR_OK;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  std::string err;
+};
+
+struct ServerSlot {
+  cudaStream_t stream = nullptr;
+  void* dbuf = nullptr;
+  int64_t dcap = 0;
+  std::thread th;
+};
+
+}  // namespace
+
+struct amr_ctx {
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  DeviceTree tree;
+  amr_options opt{8, 4, 256, 0, 1, 0};
+  std::mutex launch_mu;  // guards slots and stats
+  std::vector<LaunchSlot> slots;
+  size_t next_slot = 0;
+  void* stage = nullptr;  // device staging for host-output renders
+  int64_t stage_cap = 0;
+  // stats
+  int64_t n_renders = 0, n_cams = 0, n_rays = 0;
+  unsigned long long n_segments = 0;
+  int64_t n_dev_errors = 0;
+  double last_batch_ms = 0.0;
+  double autotune_ms = -1.0;
+  // server
+  std::mutex srv_mu;
+  std::condition_variable srv_cv;   // work arrived / budget freed / stop
+  std::condition_variable done_cv;  // a request finished
+  std::map<uint64_t, std::shared_ptr<Request>> reqs;
+  std::deque<std::shared_ptr<Request>> queue;
+  uint64_t next_ticket = 1;
+  int srv_slots = 2;
+  int64_t srv_budget = int64_t(1) << 30;
+  int64_t srv_used = 0;
+  int srv_max_batch = 64;
+  int srv_max_queue = 1 << 16;
+  bool srv_started = false;
+  bool srv_stop = false;
+  std::vector<std::unique_ptr<ServerSlot>> srv;
+  std::vector<double> latencies_ms;
+  int64_t srv_batches = 0, srv_done = 0, srv_failed = 0, srv_max_inflight = 0, srv_inflight = 0;
+  std::chrono::steady_clock::time_point srv_t0, srv_tlast;
+};
+
+namespace {
+
+constexpr int kSlots = 8;
+
+void free_slot(LaunchSlot& s) {
+  if (s.h_cams) cudaFreeHost(s.h_cams);
+  if (s.h_tiles) cudaFreeHost(s.h_tiles);
+  if (s.h_q) cudaFreeHost(s.h_q);
+  if (s.d_cams) cudaFree(s.d_cams);
+  if (s.d_tiles) cudaFree(s.d_tiles);
+  if (s.d_q) cudaFree(s.d_q);
+  s = LaunchSlot{};
+}
+
+amr_status grow_slot(LaunchSlot& s, int n) {
+  if (s.cap >= n && s.h_cams) return AMR_OK;
+  int cap = std::max(n, std::max(64, s.cap * 2));
+  if (s.h_cams) cudaFreeHost(s.h_cams);
+  if (s.h_tiles) cudaFreeHost(s.h_tiles);
+  if (s.d_cams) cudaFree(s.d_cams);
+  if (s.d_tiles) cudaFree(s.d_tiles);
+  s.h_cams = nullptr; s.h_tiles = nullptr; s.d_cams = nullptr; s.d_tiles = nullptr;
+  size_t tiles = (size_t)amr::kMaxPrecisions * (cap + 1) * sizeof(int32_t);
+  if (cudaMallocHost((void**)&s.h_cams, cap * sizeof(CamDev)) != cudaSuccess ||
+      cudaMallocHost((void**)&s.h_tiles, tiles) != cudaSuccess ||
+      cudaMalloc((void**)&s.d_cams, cap * sizeof(CamDev)) != cudaSuccess ||
+      cudaMalloc((void**)&s.d_tiles, tiles) != cudaSuccess) {
+    cudaGetLastError();
+    s.cap = 0;
+    return fail(AMR_E_OOM, "cannot allocate launch scratch for %d cameras", n);
+  }
+  s.cap = cap;
+  return AMR_OK;
+}
+
+amr_status init_slots(amr_ctx* ctx) {
+  ctx->slots.resize(kSlots);
+  for (auto& s : ctx->slots) {
+    CUDA_TRY(cudaMallocHost((void**)&s.h_q, amr::kMaxPrecisions * sizeof(QueueBlock)));
+    CUDA_TRY(cudaMalloc((void**)&s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock)));
+    CUDA_TRY(cudaEventCreate(&s.start));
+    CUDA_TRY(cudaEventCreate(&s.done));
+    std::memset(s.h_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock));
+    amr_status st = grow_slot(s, 64);
+    if (st != AMR_OK) return st;
+  }
+  return AMR_OK;
+}
+
+// Fold a finished launch's counters into the context (launch_mu held).
+amr_status harvest(amr_ctx* ctx, LaunchSlot& s) {
+  if (!s.pending) return AMR_OK;
+  s.pending = false;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, s.start, s.done) == cudaSuccess) ctx->last_batch_ms = ms;
+  else cudaGetLastError();
+  amr_status st = AMR_OK;
+  for (int g = 0; g < s.n_groups; ++g) {
+    ctx->n_segments += s.h_q[g].segments;
+    if (s.h_q[g].error != amr::kDevOk) {
+      ctx->n_dev_errors++;
+      st = fail(AMR_E_CUDA, "kernel reported error %d (oct %d)", s.h_q[g].error, s.h_q[g].err_oct);
+    }
+  }
+  return st;
+}
+
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+bool finite3(const double* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+// Pixel centre as the kernels compute it (host compiled without contraction).
+void pixel_centre(const amr_camera& c, int i, int j, double x[3]) {
+  double s = (((double)i + 0.5) / (double)c.nx - 0.5) * c.fov[0];
+  double t = (((double)j + 0.5) / (double)c.ny - 0.5) * c.fov[1];
+  for (int a = 0; a < 3; ++a) {
+    double p = c.centre[a] + s * c.u[a];
+    x[a] = p + t * c.v[a];
+  }
+}
+
+// Camera -> the constants its rays need (Sec. 2: the camera fixes the deepest
+// level read).  Returns AMR_E_INVALID with a message on a bad camera.
+amr_status canonicalise(const amr_ctx* ctx, const amr_camera& c, int tile_w, int tile_h, CamDev& d) {
+  const DeviceTree& t = ctx->tree;
+  if (!t.rec) return fail(AMR_E_INVALID, "no octree loaded");
+  if (c.nx <= 0 || c.ny <= 0 || (int64_t)c.nx * c.ny >= (int64_t(1) << 31))
+    return fail(AMR_E_INVALID, "map size %d x %d out of range", c.nx, c.ny);
+  if (c.mode < AMR_MODE_COLUMN || c.mode > AMR_MODE_MAX) return fail(AMR_E_INVALID, "unknown mode %d", c.mode);
+  if (c.precision < AMR_PREC_FP64 || c.precision > AMR_PREC_FP32_PLAIN)
+    return fail(AMR_E_INVALID, "unknown precision %d", c.precision);
+  const int nf = (int)t.fields.size();
+  auto fok = [nf](int f) { return f >= 0 && f < nf; };
+  if (c.mode == AMR_MODE_WMEAN) {
+    if (!fok(c.field_weight) || !fok(c.field_vel[0]) || !fok(c.field_vel[1]) || !fok(c.field_vel[2]))
+      return fail(AMR_E_INVALID, "wmean needs a weight field and 3 velocity fields (tree has %d fields)", nf);
+  } else if (!fok(c.field_value)) {
+    return fail(AMR_E_INVALID, "field %d out of range (tree has %d fields)", c.field_value, nf);
+  }
+  if (!finite3(c.centre) || !finite3(c.u) || !finite3(c.v) || !finite3(c.w) || !std::isfinite(c.fov[0]) ||
+      !std::isfinite(c.fov[1]) || !(c.fov[0] > 0.0) || !(c.fov[1] > 0.0))
+    return fail(AMR_E_INVALID, "camera has a non-finite value or a non-positive field of view");
+  const double tol = 1e-9;
+  if (std::fabs(dot3(c.u, c.u) - 1.0) > tol || std::fabs(dot3(c.v, c.v) - 1.0) > tol ||
+      std::fabs(dot3(c.w, c.w) - 1.0) > tol || std::fabs(dot3(c.u, c.v)) > tol || std::fabs(dot3(c.u, c.w)) > tol ||
+      std::fabs(dot3(c.v, c.w)) > tol)
+    return fail(AMR_E_INVALID, "camera axes u, v, w are not orthonormal to 1e-9");
+  int L;
+  if (c.max_level > 0) {
+    L = c.max_level;
+  } else if (c.max_level == AMR_LEVEL_AUTO) {
+    // deepest l with 2^-l >= fov_a / n_a, i.e. fov_a * 2^l <= n_a (exact in double)
+    L = 1;
+    while (L < amr::kMaxLevel && std::ldexp(c.fov[0], L + 1) <= (double)c.nx &&
+           std::ldexp(c.fov[1], L + 1) <= (double)c.ny)
+      ++L;
+  } else {
+    return fail(AMR_E_INVALID, "max_level %d: use > 0 or AMR_LEVEL_AUTO", c.max_level);
+  }
+  L = std::max(1, std::min(L, t.depth));
+  // The four corner pixels bound every pixel centre (the formula is monotone in i and j).
+  const int ci[2] = {0, c.nx - 1}, cj[2] = {0, c.ny - 1};
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) {
+      double x[3];
+      pixel_centre(c, ci[p], cj[q], x);
+      for (int a = 0; a < 3; ++a)
+        if (!(x[a] >= -1.0 && x[a] <= 2.0))
+          return fail(AMR_E_INVALID, "pixel centres leave [-1, 2]^3 (axis %d: %.17g)", a, x[a]);
+    }
+  std::memset(&d, 0, sizeof d);
+  const double wm = std::fmax(std::fabs(c.w[0]), std::fmax(std::fabs(c.w[1]), std::fabs(c.w[2])));
+  double s2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    long long q = std::llrint(std::ldexp(c.w[a] / wm, amr::kDirBits));
+    d.D[a] = (int32_t)q;
+    s2 += (double)q * (double)q;
+  }
+  d.lam = std::ldexp(std::sqrt(s2), -amr::kFixBits);
+  for (int a = 0; a < 3; ++a) {
+    const double ad = std::fabs((double)d.D[a]);
+    d.invD[a] = ad > 0 ? 1.0 / ad : 0.0;
+    d.lamInv[a] = ad > 0 ? d.lam / ad : 0.0;
+    d.invDF[a] = (float)d.invD[a];
+    d.lamInvF[a] = (float)d.lamInv[a];
+    d.centre[a] = c.centre[a];
+    d.u[a] = c.u[a];
+    d.v[a] = c.v[a];
+    d.w[a] = c.w[a];
+    d.wF[a] = (float)c.w[a];
+  }
+  d.fov0 = c.fov[0];
+  d.fov1 = c.fov[1];
+  d.nxd = (double)c.nx;
+  d.nyd = (double)c.ny;
+  d.nx = c.nx;
+  d.ny = c.ny;
+  d.L = L;
+  d.mode = c.mode;
+  d.tiles_x = (c.nx + tile_w - 1) / tile_w;
+  if (c.mode == AMR_MODE_WMEAN) {
+    d.rho = t.fields[c.field_weight];
+    for (int a = 0; a < 3; ++a) d.vel[a] = t.fields[c.field_vel[a]];
+  } else {
+    d.rho = t.fields[c.field_value];
+  }
+  (void)tile_h;
+  return AMR_OK;
+}
+
+int64_t tiles_of(const CamDev& d, int tile_w, int tile_h) {
+  return (int64_t)((d.nx + tile_w - 1) / tile_w) * ((d.ny + tile_h - 1) / tile_h);
+}
+
+int64_t map_bytes(const amr_camera& c) {
+  return (int64_t)c.nx * c.ny * (c.precision == AMR_PREC_FP64 ? 8 : 4);
+}
+
+amr_status check_options(const amr_options& o) {
+  if (o.tile_w < 1 || o.tile_h < 1 || o.tile_w * o.tile_h != 32)
+    return fail(AMR_E_INVALID, "tile %d x %d: tile_w * tile_h must be 32", o.tile_w, o.tile_h);
+  if (o.block_threads < 64 || o.block_threads > 256 || o.block_threads % 32)
+    return fail(AMR_E_INVALID, "block_threads %d: use 64..256, a multiple of 32", o.block_threads);
+  if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return fail(AMR_E_INVALID, "blocks_per_sm %d", o.blocks_per_sm);
+  if (o.tiles_per_grab < 1 || o.tiles_per_grab > 64) return fail(AMR_E_INVALID, "tiles_per_grab %d", o.tiles_per_grab);
+  return AMR_OK;
+}
+
+// Enqueue one batch of canonical cameras (map/count pointers already device
+// pointers) on `stream`: one persistent launch per precision present.
+amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDev>& cams,
+                   const std::vector<int>& precs, cudaStream_t stream, LaunchSlot** used) {
+  std::unique_lock<std::mutex> lk(ctx->launch_mu);
+  LaunchSlot& s = ctx->slots[ctx->next_slot];
+  ctx->next_slot = (ctx->next_slot + 1) % ctx->slots.size();
+  if (s.pending) {
+    CUDA_TRY(cudaEventSynchronize(s.done));
+    harvest(ctx, s);
+  }
+  const int n = (int)cams.size();
+  amr_status st = grow_slot(s, n);
+  if (st != AMR_OK) return st;
+  // Order cameras by precision group; each group gets its own prefix table.
+  int groups[amr::kMaxPrecisions] = {0, 0, 0};
+  int gstart[amr::kMaxPrecisions + 1] = {0, 0, 0, 0};
+  for (int p : precs) groups[p]++;
+  for (int g = 0; g < amr::kMaxPrecisions; ++g) gstart[g + 1] = gstart[g] + groups[g];
+  int fill[amr::kMaxPrecisions] = {gstart[0], gstart[1], gstart[2]};
+  for (int i = 0; i < n; ++i) s.h_cams[fill[precs[i]]++] = cams[i];
+  int64_t tiles_total[amr::kMaxPrecisions] = {0, 0, 0};
+  for (int g = 0; g < amr::kMaxPrecisions; ++g) {
+    int32_t* tp = s.h_tiles + (size_t)g * (s.cap + 1);
+    int64_t acc = 0;
+    for (int i = 0; i < groups[g]; ++i) {
+      tp[i] = (int32_t)acc;
+      acc += tiles_of(s.h_cams[gstart[g] + i], opt.tile_w, opt.tile_h);
+    }
+    tp[groups[g]] = (int32_t)acc;
+    if (acc >= (int64_t(1) << 31) - 4096) return fail(AMR_E_INVALID, "batch too large: %lld tiles", (long long)acc);
+    tiles_total[g] = acc;
+  }
+  CUDA_TRY(cudaEventRecord(s.start, stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_cams, s.h_cams, n * sizeof(CamDev), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_tiles, s.h_tiles, (size_t)amr::kMaxPrecisions * (s.cap + 1) * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), stream));
+  s.n_groups = amr::kMaxPrecisions;
+  for (int g = 0; g < amr::kMaxPrecisions; ++g) {
+    if (!groups[g] || !tiles_total[g]) continue;
+    amr::BatchArgs a{};
+    a.rec = ctx->tree.rec;
+    a.n_oct = (uint32_t)ctx->tree.n_oct;
+    a.n_cams = groups[g];
+    a.cams = s.d_cams + gstart[g];
+    a.tile_start = s.d_tiles + (size_t)g * (s.cap + 1);
+    a.total_tiles = (int32_t)tiles_total[g];
+    a.tile_w = opt.tile_w;
+    a.tile_h = opt.tile_h;
+    a.tiles_per_grab = opt.tiles_per_grab;
+    a.q = s.d_q + g;
+    int bps = opt.blocks_per_sm;
+    if (bps <= 0) {
+      CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, opt.block_threads, &bps));
+      bps = std::max(1, bps);
+    }
+    int64_t grid = (int64_t)ctx->sms * bps;
+    const int64_t warps_needed = (tiles_total[g] + opt.tiles_per_grab - 1) / opt.tiles_per_grab;
+    const int64_t blocks_needed = (warps_needed * 32 + opt.block_threads - 1) / opt.block_threads;
+    grid = std::max<int64_t>(1, std::min(grid, blocks_needed));
+    CUDA_TRY(amr::launch_batch(g, ctx->tree.f64, a, (int)grid, opt.block_threads, stream));
+  }
+  CUDA_TRY(cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaEventRecord(s.done, stream));
+  s.pending = true;
+  ctx->n_renders++;
+  ctx->n_cams += n;
+  for (const CamDev& c : cams) ctx->n_rays += (int64_t)c.nx * c.ny;
+  if (used) *used = &s;
+  return AMR_OK;
+}
+
+amr_status finish_sync(amr_ctx* ctx, LaunchSlot* s) {
+  CUDA_TRY(cudaEventSynchronize(s->done));
+  std::lock_guard<std::mutex> lk(ctx->launch_mu);
+  return harvest(ctx, *s);
+}
+
+amr_status ensure_stage(amr_ctx* ctx, int64_t bytes) {
+  if (ctx->stage_cap >= bytes) return AMR_OK;
+  if (ctx->stage) cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_cap = 0;
+  if (cudaMalloc(&ctx->stage, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AMR_E_OOM, "cannot allocate %lld bytes of output staging", (long long)bytes);
+  }
+  ctx->stage_cap = bytes;
+  return AMR_OK;
+}
+
+amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps, int32_t* const* counts,
+                       int out_on_device, void* cuda_stream) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  if (n < 0 || (n > 0 && (!cams || !maps))) return fail(AMR_E_INVALID, "bad batch arguments");
+  if (n == 0) return AMR_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const amr_options opt = ctx->opt;
+  std::vector<CamDev> dev(n);
+  std::vector<int> precs(n);
+  int64_t stage_bytes = 0;
+  std::vector<int64_t> off(n);
+  for (int i = 0; i < n; ++i) {
+    amr_status st = canonicalise(ctx, cams[i], opt.tile_w, opt.tile_h, dev[i]);
+    if (st != AMR_OK) return fail(st, "camera %d: %s", i, g_err.c_str());
+    if (!maps[i]) return fail(AMR_E_INVALID, "camera %d: null map pointer", i);
+    precs[i] = cams[i].precision;
+    off[i] = stage_bytes;
+    const int64_t px = (int64_t)cams[i].nx * cams[i].ny;
+    stage_bytes += ((map_bytes(cams[i]) + 255) / 256) * 256;
+    if (counts && counts[i]) stage_bytes += ((px * 4 + 255) / 256) * 256;
+  }
+  cudaStream_t stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  if (out_on_device) {
+    for (int i = 0; i < n; ++i) {
+      dev[i].map = maps[i];
+      dev[i].counts = counts ? counts[i] : nullptr;
+    }
+    LaunchSlot* s = nullptr;
+    return enqueue(ctx, opt, dev, precs, stream, &s);
+  }
+  amr_status st = ensure_stage(ctx, stage_bytes);
+  if (st != AMR_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    char* base = (char*)ctx->stage + off[i];
+    dev[i].map = base;
+    dev[i].counts = (counts && counts[i]) ? (int32_t*)(base + ((map_bytes(cams[i]) + 255) / 256) * 256) : nullptr;
+  }
+  LaunchSlot* s = nullptr;
+  st = enqueue(ctx, opt, dev, precs, stream, &s);
+  if (st != AMR_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    CUDA_TRY(cudaMemcpyAsync(maps[i], dev[i].map, (size_t)map_bytes(cams[i]), cudaMemcpyDeviceToHost, stream));
+    if (dev[i].counts)
+      CUDA_TRY(cudaMemcpyAsync(counts[i], dev[i].counts, (size_t)cams[i].nx * cams[i].ny * 4, cudaMemcpyDeviceToHost,
+                               stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return finish_sync(ctx, s);
+}
+
+// ------------------------------------------------------------------ server
+void complete(amr_ctx* ctx, const std::vector<std::shared_ptr<Request>>& batch, amr_status st, const char* err) {
+  auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(ctx->srv_mu);
+  for (auto& r : batch) {
+    r->status = st;
+    if (err) r->err = err;
+    r->state = 2;
+    r->t_done = now;
+    ctx->srv_used -= r->bytes;
+    if (st == AMR_OK) {
+      ctx->srv_done++;
+      ctx->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+    } else {
+      ctx->srv_failed++;
+    }
+  }
+  ctx->srv_inflight--;
+  ctx->srv_tlast = now;
+  ctx->done_cv.notify_all();
+  ctx->srv_cv.notify_all();
+}
+
+void server_worker(amr_ctx* ctx, ServerSlot* slot) {
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> batch;
+    {
+      std::unique_lock<std::mutex> lk(ctx->srv_mu);
+      ctx->srv_cv.wait(lk, [&] {
+        if (ctx->srv_stop) return true;
+        if (ctx->queue.empty()) return false;
+        return ctx->srv_used + ctx->queue.front()->bytes <= ctx->srv_budget || ctx->srv_used == 0;
+      });
+      if (ctx->srv_stop) return;
+      // Admit in arrival order while slots' memory budget allows.
+      while (!ctx->queue.empty() && (int)batch.size() < ctx->srv_max_batch) {
+        auto& r = ctx->queue.front();
+        if (ctx->srv_used + r->bytes > ctx->srv_budget && !(batch.empty() && ctx->srv_used == 0)) break;
+        ctx->srv_used += r->bytes;
+        r->state = 1;
+        batch.push_back(r);
+        ctx->queue.pop_front();
+      }
+      ctx->srv_batches++;
+      ctx->srv_inflight++;
+      ctx->srv_max_inflight = std::max(ctx->srv_max_inflight, ctx->srv_inflight);
+    }
+    // Device outputs in this slot's buffer, then copies into the callers' buffers.
+    int64_t need = 0;
+    std::vector<int64_t> off(batch.size());
+    for (size_t i = 0; i < batch.size(); ++i) {
+      off[i] = need;
+      need += ((batch[i]->bytes + 255) / 256) * 256;
+    }
+    amr_status st = AMR_OK;
+    std::string err;
+    if (need > slot->dcap) {
+      if (slot->dbuf) cudaFree(slot->dbuf);
+      slot->dbuf = nullptr;
+      slot->dcap = 0;
+      if (cudaMalloc(&slot->dbuf, (size_t)need) != cudaSuccess) {
+        cudaGetLastError();
+        st = AMR_E_OOM;
+        err = "server slot buffer allocation failed";
+      } else {
+        slot->dcap = need;
+      }
+    }
+    if (st == AMR_OK) {
+      std::vector<amr_camera> cams(batch.size());
+      std::vector<void*> maps(batch.size());
+      std::vector<int32_t*> cnts(batch.size());
+      for (size_t i = 0; i < batch.size(); ++i) {
+        cams[i] = batch[i]->cam;
+        maps[i] = (char*)slot->dbuf + off[i];
+        const int64_t mb = map_bytes(cams[i]);
+        cnts[i] = batch[i]->counts ? (int32_t*)((char*)maps[i] + ((mb + 255) / 256) * 256) : nullptr;
+      }
+      st = render_impl(ctx, (int32_t)batch.size(), cams.data(), maps.data(), cnts.data(), 1, slot->stream);
+      if (st == AMR_OK) {
+        for (size_t i = 0; i < batch.size() && st == AMR_OK; ++i) {
+          if (cudaMemcpyAsync(batch[i]->map, maps[i], (size_t)map_bytes(cams[i]), cudaMemcpyDeviceToHost,
+                              slot->stream) != cudaSuccess)
+            st = AMR_E_CUDA;
+          if (cnts[i] && cudaMemcpyAsync(batch[i]->counts, cnts[i], (size_t)cams[i].nx * cams[i].ny * 4,
+                                         cudaMemcpyDeviceToHost, slot->stream) != cudaSuccess)
+            st = AMR_E_CUDA;
+        }
+        if (cudaStreamSynchronize(slot->stream) != cudaSuccess) st = AMR_E_CUDA;
+        if (st != AMR_OK) err = cudaGetErrorString(cudaGetLastError());
+      } else {
+        err = g_err;
+      }
+    }
+    complete(ctx, batch, st, err.empty() ? nullptr : err.c_str());
+  }
+}
+
+amr_status start_server(amr_ctx* ctx) {
+  if (ctx->srv_started) return AMR_OK;
+  for (int i = 0; i < ctx->srv_slots; ++i) {
+    auto s = std::make_unique<ServerSlot>();
+    CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    ctx->srv.push_back(std::move(s));
+  }
+  for (auto& s : ctx->srv) s->th = std::thread(server_worker, ctx, s.get());
+  ctx->srv_started = true;
+  ctx->srv_t0 = std::chrono::steady_clock::now();
+  return AMR_OK;
+}
+
+// Breadth-first renumbering with validation.  order[new] = old oct index.
+amr_status linearise(int64_t n, const uint8_t* level, const int32_t* coord, const int32_t* child,
+                     std::vector<int32_t>& order, std::vector<uint2>& rec, int& depth) {
+  if (level[0] != 1 || coord[0] != 0 || coord[1] != 0 || coord[2] != 0)
+    return fail(AMR_E_BADTREE, "oct 0 must be the root: level 1, coord (0,0,0)");
+  std::vector<int32_t> seen((size_t)n, -1);
+  order.clear();
+  order.reserve((size_t)n);
+  order.push_back(0);
+  seen[0] = 0;
+  depth = 1;
+  for (size_t p = 0; p < order.size(); ++p) {
+    const int64_t o = order[p];
+    const int lv = level[o];
+    if (lv < 1 || lv > amr::kMaxLevel) return fail(AMR_E_BADTREE, "oct %lld: level %d out of [1, 22]", (long long)o, lv);
+    depth = std::max(depth, lv);
+    const int64_t lim = int64_t(1) << lv;
+    for (int a = 0; a < 3; ++a) {
+      const int64_t k = coord[3 * o + a];
+      if (k < 0 || k + 1 >= lim + 1 || (k & 1))
+        return fail(AMR_E_BADTREE, "oct %lld: coordinate %lld out of range or odd at level %d", (long long)o,
+                    (long long)k, lv);
+    }
+    for (int c = 0; c < 8; ++c) {
+      const int64_t ch = child[8 * o + c];
+      if (ch == -1) continue;
+      if (ch <= 0 || ch >= n) return fail(AMR_E_BADTREE, "oct %lld cell %d: child index %lld out of range", (long long)o, c, (long long)ch);
+      if (seen[ch] != -1) return fail(AMR_E_BADTREE, "oct %lld: referenced more than once (cycle or shared child)", (long long)ch);
+      if (level[ch] != lv + 1)
+        return fail(AMR_E_BADTREE, "oct %lld: level %d but its parent oct %lld has level %d", (long long)ch, level[ch], (long long)o, lv);
+      for (int a = 0; a < 3; ++a)
+        if (coord[3 * ch + a] != 2 * (coord[3 * o + a] + ((c >> a) & 1)))
+          return fail(AMR_E_BADTREE, "oct %lld: coordinates do not match cell %d of parent oct %lld", (long long)ch, c, (long long)o);
+      seen[ch] = (int32_t)order.size();
+      order.push_back((int32_t)ch);
+    }
+  }
+  if ((int64_t)order.size() != n) {
+    for (int64_t o = 0; o < n; ++o)
+      if (seen[o] == -1) return fail(AMR_E_BADTREE, "oct %lld: not reachable from the root", (long long)o);
+  }
+  rec.assign((size_t)n, uint2{0u, 0u});
+  for (int64_t p = 0; p < n; ++p) {
+    const int64_t o = order[p];
+    uint32_t mask = 0, base = 0;
+    bool have = false;
+    for (int c = 0; c < 8; ++c) {
+      const int32_t ch = child[8 * o + c];
+      if (ch < 0) continue;
+      mask |= 1u << c;
+      if (!have) { base = (uint32_t)seen[ch]; have = true; }
+    }
+    rec[p] = uint2{base, mask};
+  }
+  return AMR_OK;
+}
+
+void free_tree(DeviceTree& t) {
+  if (t.rec) cudaFree(t.rec);
+  for (void* f : t.fields) if (f) cudaFree(f);
+  t = DeviceTree{};
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_create(amr_ctx** out, int device) {
+  if (!out) return fail(AMR_E_INVALID, "null output pointer");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(AMR_E_INVALID, "device %d of %d", device, ndev);
+  CUDA_TRY(cudaSetDevice(device));
+  amr_ctx* ctx = new (std::nothrow) amr_ctx;
+  if (!ctx) return fail(AMR_E_OOM, "host allocation failed");
+  ctx->device = device;
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return fail(AMR_E_CUDA, "device set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  ctx->sms = prop.multiProcessorCount;
+  amr_status st = init_slots(ctx);
+  if (st != AMR_OK) {
+    amr_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return AMR_OK;
+}
+
+amr_status amr_destroy(amr_ctx* ctx) {
+  if (!ctx) return AMR_OK;
+  cudaSetDevice(ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(ctx->srv_mu);
+    ctx->srv_stop = true;
+    for (auto& r : ctx->queue) {
+      r->status = AMR_E_CANCELLED;
+      r->state = 2;
+    }
+    ctx->queue.clear();
+  }
+  ctx->srv_cv.notify_all();
+  ctx->done_cv.notify_all();
+  for (auto& s : ctx->srv) {
+    if (s->th.joinable()) s->th.join();
+    if (s->dbuf) cudaFree(s->dbuf);
+    if (s->stream) cudaStreamDestroy(s->stream);
+  }
+  ctx->srv.clear();
+  cudaDeviceSynchronize();
+  for (auto& s : ctx->slots) {
+    if (s.start) cudaEventDestroy(s.start);
+    if (s.done) cudaEventDestroy(s.done);
+    free_slot(s);
+  }
+  free_tree(ctx->tree);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return AMR_OK;
+}
+
+amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, const int32_t* coord,
+                           const int32_t* child, int32_t n_fields, const void* const* fields, int32_t field_dtype) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  if (n_oct < 1 || n_oct > (int64_t)0x7fffffff / 8) return fail(AMR_E_INVALID, "n_oct %lld out of range", (long long)n_oct);
+  if (!level || !coord || !child) return fail(AMR_E_INVALID, "null tree array");
+  if (n_fields < 1 || n_fields > 64 || !fields) return fail(AMR_E_INVALID, "n_fields %d: need 1..64 fields", n_fields);
+  for (int f = 0; f < n_fields; ++f)
+    if (!fields[f]) return fail(AMR_E_INVALID, "field %d is null", f);
+  if (field_dtype != AMR_F32 && field_dtype != AMR_F64) return fail(AMR_E_INVALID, "field dtype %d", field_dtype);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  std::vector<int32_t> order;
+  std::vector<uint2> rec;
+  int depth = 1;
+  amr_status st;
+  try {
+    st = linearise(n_oct, level, coord, child, order, rec, depth);
+  } catch (const std::bad_alloc&) {
+    return fail(AMR_E_OOM, "host memory for linearisation");
+  }
+  if (st != AMR_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  {
+    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+    for (auto& s : ctx->slots)
+      if (s.pending) {
+        cudaEventSynchronize(s.done);
+        harvest(ctx, s);
+      }
+  }
+  free_tree(ctx->tree);
+  DeviceTree t;
+  const size_t esz = field_dtype == AMR_F64 ? 8 : 4;
+  const size_t fbytes = (size_t)n_oct * 8 * esz;
+  if (cudaMalloc((void**)&t.rec, (size_t)n_oct * sizeof(uint2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AMR_E_OOM, "device memory for %lld oct records", (long long)n_oct);
+  }
+  t.fields.assign(n_fields, nullptr);
+  for (int f = 0; f < n_fields; ++f) {
+    if (cudaMalloc(&t.fields[f], fbytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_tree(t);
+      return fail(AMR_E_OOM, "device memory for field %d (%zu bytes)", f, fbytes);
+    }
+  }
+  cudaError_t e = cudaMemcpy(t.rec, rec.data(), (size_t)n_oct * sizeof(uint2), cudaMemcpyHostToDevice);
+  std::vector<char> buf;
+  try {
+    buf.resize(fbytes);
+  } catch (const std::bad_alloc&) {
+    free_tree(t);
+    return fail(AMR_E_OOM, "host memory for field permutation");
+  }
+  for (int f = 0; f < n_fields && e == cudaSuccess; ++f) {
+    const char* src = (const char*)fields[f];
+    for (int64_t p = 0; p < n_oct; ++p) std::memcpy(&buf[(size_t)p * 8 * esz], src + (size_t)order[p] * 8 * esz, 8 * esz);
+    e = cudaMemcpy(t.fields[f], buf.data(), fbytes, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    free_tree(t);
+    return fail(AMR_E_CUDA, "tree upload: %s", cudaGetErrorString(e));
+  }
+  t.n_oct = n_oct;
+  t.depth = depth;
+  t.f64 = field_dtype == AMR_F64;
+  t.bytes = (int64_t)(n_oct * sizeof(uint2) + n_fields * fbytes);
+  ctx->tree = std::move(t);
+  return AMR_OK;
+}
+
+amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* count_out, int out_on_device,
+                      void* cuda_stream) {
+  if (!cam || !map_out) return fail(AMR_E_INVALID, "null camera or map");
+  void* maps[1] = {map_out};
+  int32_t* counts[1] = {count_out};
+  return render_impl(ctx, 1, cam, maps, counts, out_on_device, cuda_stream);
+}
+
+amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
+                            int32_t* const* counts, int out_on_device, void* cuda_stream) {
+  return render_impl(ctx, n, cams, maps, counts, out_on_device, cuda_stream);
+}
+
+amr_status amr_camera_check(amr_ctx* ctx, const amr_camera* cam, int32_t* level_out) {
+  if (!ctx || !cam) return fail(AMR_E_INVALID, "null argument");
+  CamDev d;
+  amr_status st = canonicalise(ctx, *cam, ctx->opt.tile_w, ctx->opt.tile_h, d);
+  if (st == AMR_OK && level_out) *level_out = d.L;
+  return st;
+}
+
+amr_status amr_set_options(amr_ctx* ctx, const amr_options* opt) {
+  if (!ctx || !opt) return fail(AMR_E_INVALID, "null argument");
+  amr_status st = check_options(*opt);
+  if (st != AMR_OK) return st;
+  ctx->opt = *opt;
+  return AMR_OK;
+}
+
+amr_status amr_get_options(amr_ctx* ctx, amr_options* opt) {
+  if (!ctx || !opt) return fail(AMR_E_INVALID, "null argument");
+  *opt = ctx->opt;
+  return AMR_OK;
+}
+
+amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t reps, amr_options* best,
+                        double* ms_out) {
+  if (!ctx || n <= 0 || !cams || reps < 1) return fail(AMR_E_INVALID, "bad autotune arguments");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  // Device outputs into staging; every candidate renders the same batch.
+  int64_t bytes = 0;
+  for (int i = 0; i < n; ++i) bytes += ((map_bytes(cams[i]) + 255) / 256) * 256;
+  amr_status st = ensure_stage(ctx, bytes);
+  if (st != AMR_OK) return st;
+  std::vector<void*> maps(n);
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    maps[i] = (char*)ctx->stage + off;
+    off += ((map_bytes(cams[i]) + 255) / 256) * 256;
+  }
+  const int tiles[][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+  const int blocks[] = {128, 256};
+  const int grabs[] = {1, 4};
+  const amr_options saved = ctx->opt;
+  amr_options bestopt = saved;
+  double bestms = 1e300;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  for (auto& tl : tiles)
+    for (int bt : blocks)
+      for (int gr : grabs) {
+        amr_options o = saved;
+        o.tile_w = tl[0];
+        o.tile_h = tl[1];
+        o.block_threads = bt;
+        o.tiles_per_grab = gr;
+        o.blocks_per_sm = 0;
+        ctx->opt = o;
+        std::vector<double> times;
+        for (int r = 0; r < reps + 1 && st == AMR_OK; ++r) {
+          cudaEventRecord(e0, ctx->stream);
+          st = render_impl(ctx, n, cams, maps.data(), nullptr, 1, ctx->stream);
+          cudaEventRecord(e1, ctx->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(AMR_E_CUDA, "autotune sync failed");
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0) times.push_back(ms);  // first run warms caches
+        }
+        if (st != AMR_OK) break;
+        std::sort(times.begin(), times.end());
+        const double med = times[times.size() / 2];
+        if (med < bestms) {
+          bestms = med;
+          bestopt = o;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->opt = st == AMR_OK ? bestopt : saved;
+  if (st != AMR_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+    for (auto& s : ctx->slots)
+      if (s.pending) {
+        cudaEventSynchronize(s.done);
+        harvest(ctx, s);
+      }
+  }
+  ctx->autotune_ms = bestms;
+  if (best) *best = bestopt;
+  if (ms_out) *ms_out = bestms;
+  return AMR_OK;
+}
+
+amr_status amr_server_config(amr_ctx* ctx, int32_t slots, int64_t map_budget_bytes, int32_t max_batch) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  std::lock_guard<std::mutex> lk(ctx->srv_mu);
+  if (ctx->srv_started) return fail(AMR_E_BUSY, "server already running");
+  if (slots < 1 || slots > 8 || map_budget_bytes < 0 || max_batch < 1)
+    return fail(AMR_E_INVALID, "server config: slots 1..8, budget >= 0, max_batch >= 1");
+  ctx->srv_slots = slots;
+  ctx->srv_budget = map_budget_bytes ? map_budget_bytes : (int64_t(1) << 30);
+  ctx->srv_max_batch = max_batch;
+  return AMR_OK;
+}
+
+amr_status amr_submit(amr_ctx* ctx, const amr_camera* cam, void* map, int32_t* counts, uint64_t* ticket) {
+  if (!ctx || !cam || !map || !ticket) return fail(AMR_E_INVALID, "null argument");
+  CamDev d;
+  amr_status st = canonicalise(ctx, *cam, ctx->opt.tile_w, ctx->opt.tile_h, d);
+  if (st != AMR_OK) return st;
+  auto r = std::make_shared<Request>();
+  r->cam = *cam;
+  r->map = map;
+  r->counts = counts;
+  r->bytes = ((map_bytes(*cam) + 255) / 256) * 256 + (counts ? (((int64_t)cam->nx * cam->ny * 4 + 255) / 256) * 256 : 0);
+  r->t_submit = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(ctx->srv_mu);
+  if (ctx->srv_stop) return fail(AMR_E_CANCELLED, "context is shutting down");
+  if ((int)ctx->queue.size() >= ctx->srv_max_queue) return fail(AMR_E_BUSY, "request queue full");
+  if (r->bytes > ctx->srv_budget) return fail(AMR_E_OOM, "request needs %lld bytes, budget %lld", (long long)r->bytes, (long long)ctx->srv_budget);
+  if (!ctx->srv_started) {
+    st = start_server(ctx);
+    if (st != AMR_OK) return st;
+  }
+  *ticket = ctx->next_ticket++;
+  ctx->reqs[*ticket] = r;
+  ctx->queue.push_back(r);
+  ctx->srv_cv.notify_one();
+  return AMR_OK;
+}
+
+amr_status amr_wait(amr_ctx* ctx, uint64_t ticket, int64_t timeout_us) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  std::unique_lock<std::mutex> lk(ctx->srv_mu);
+  auto it = ctx->reqs.find(ticket);
+  if (it == ctx->reqs.end()) return fail(AMR_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+  std::shared_ptr<Request> r = it->second;
+  auto pred = [&] { return r->state == 2; };
+  if (timeout_us < 0) {
+    ctx->done_cv.wait(lk, pred);
+  } else if (!ctx->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), pred)) {
+    return fail(AMR_E_TIMEOUT, "ticket %llu not finished after %lld us", (unsigned long long)ticket, (long long)timeout_us);
+  }
+  ctx->reqs.erase(ticket);
+  if (r->status != AMR_OK) return fail(r->status, "request %llu failed: %s", (unsigned long long)ticket, r->err.c_str());
+  return AMR_OK;
+}
+
+amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  std::lock_guard<std::mutex> lk(ctx->srv_mu);
+  auto it = ctx->reqs.find(ticket);
+  if (it == ctx->reqs.end()) return fail(AMR_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+  auto r = it->second;
+  if (r->state != 0) return fail(AMR_E_BUSY, "ticket %llu already running or done", (unsigned long long)ticket);
+  for (auto q = ctx->queue.begin(); q != ctx->queue.end(); ++q)
+    if (q->get() == r.get()) {
+      ctx->queue.erase(q);
+      break;
+    }
+  r->status = AMR_E_CANCELLED;
+  r->err = "cancelled";
+  r->state = 2;
+  ctx->done_cv.notify_all();
+  return AMR_OK;
+}
+
+amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
+  if (!ctx || !json_buf || buf_len <= 0) return fail(AMR_E_INVALID, "bad arguments");
+  cudaSetDevice(ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+    for (auto& s : ctx->slots)
+      if (s.pending && cudaEventQuery(s.done) == cudaSuccess) harvest(ctx, s);
+    cudaGetLastError();
+  }
+  double p50 = 0, p99 = 0, fps = 0;
+  int64_t done, failed, batches, maxin, queued;
+  {
+    std::lock_guard<std::mutex> lk(ctx->srv_mu);
+    std::vector<double> l = ctx->latencies_ms;
+    if (!l.empty()) {
+      std::sort(l.begin(), l.end());
+      p50 = l[(size_t)(0.50 * (l.size() - 1))];
+      p99 = l[(size_t)(0.99 * (l.size() - 1))];
+      const double span = std::chrono::duration<double>(ctx->srv_tlast - ctx->srv_t0).count();
+      fps = span > 0 ? l.size() / span : 0.0;
+    }
+    done = ctx->srv_done;
+    failed = ctx->srv_failed;
+    batches = ctx->srv_batches;
+    maxin = ctx->srv_max_inflight;
+    queued = (int64_t)ctx->queue.size();
+  }
+  const amr_options& o = ctx->opt;
+  const bool f64 = ctx->tree.f64;
+  char buf[2048];
+  int len = std::snprintf(
+      buf, sizeof buf,
+      "{\"renders\": %lld, \"cameras\": %lld, \"rays\": %lld, \"segments\": %llu, \"device_errors\": %lld, "
+      "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d}, "
+      "\"options\": {\"tile_w\": %d, \"tile_h\": %d, \"block_threads\": %d, \"blocks_per_sm\": %d, "
+      "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, "
+      "\"regs\": {\"fp64\": %d, \"fp32_kahan\": %d, \"fp32_plain\": %d}, \"sms\": %d, "
+      "\"server\": {\"done\": %lld, \"failed\": %lld, \"batches\": %lld, \"max_inflight\": %lld, \"queued\": %lld, "
+      "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
+      (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
+      (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
+      (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
+      o.use_graph, ctx->autotune_ms, amr::batch_regs(0, f64), amr::batch_regs(1, f64), amr::batch_regs(2, f64),
+      ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
+      fps);
+  if (len < 0) return fail(AMR_E_INVALID, "stats formatting failed");
+  int64_t n = std::min<int64_t>(len, buf_len - 1);
+  std::memcpy(json_buf, buf, (size_t)n);
+  json_buf[n] = '\0';
+  return AMR_OK;
+}
+
+amr_status amr_tree_info(amr_ctx* ctx, int64_t* n_oct, int32_t* depth, int64_t* device_bytes) {
+  if (!ctx) return fail(AMR_E_INVALID, "null context");
+  if (n_oct) *n_oct = ctx->tree.n_oct;
+  if (depth) *depth = ctx->tree.depth;
+  if (device_bytes) *device_bytes = ctx->tree.bytes;
+  return AMR_OK;
+}
+
+const char* amr_last_error(amr_ctx* ctx) {
+  (void)ctx;
+  return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal types shared by the host C ABI (amr_api.cpp) and the CUDA kernels
+// (amr_kernels.cu).  Not part of the public interface.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace amr {
+
+constexpr int kFixBits = 36;      // fixed-point bits of a coordinate: level 22 + 14 guard bits
+constexpr int kDirBits = 23;      // bits of the largest quantised direction component
+constexpr int kMaxLevel = 22;     // deepest level an octree may hold
+constexpr int kMaxPrecisions = 3;
+
+// Error codes a kernel writes into the work-queue block (never traps).
+enum : int32_t { kDevOk = 0, kDevBadOct = 1, kDevStepCap = 2 };
+
+// One camera after host canonicalisation: what a warp needs to trace its tile.
+struct CamDev {
+  double centre[3], u[3], v[3], w[3];
+  double fov0, fov1;
+  double nxd, nyd;          // nx, ny as doubles (pixel-centre formula)
+  double lam;               // box length per unit of ray parameter: |D|_2 2^-36
+  double lamInv[3];         // lam / |D_a| (0 where D_a = 0)
+  double invD[3];           // 1 / |D_a| (0 where D_a = 0)
+  float lamInvF[3], invDF[3], wF[3];
+  int32_t D[3];             // quantised direction, |D_a| <= 2^23
+  int32_t nx, ny, L, mode;
+  int32_t tiles_x;
+  int32_t pad0;
+  const void* rho;          // value field (column, max) or weight field (wmean)
+  const void* vel[3];       // wmean velocity fields
+  void* map;                // float* or double* [ny][nx]
+  int32_t* counts;          // nullable
+};
+
+// Scratch block one launch owns: queue head, error word, segment counter.
+struct QueueBlock {
+  int32_t head;
+  int32_t error;
+  int32_t err_oct;
+  int32_t pad;
+  unsigned long long segments;
+};
+
+struct BatchArgs {
+  const uint2* rec;         // oct records {first child, refinement mask}
+  uint32_t n_oct;
+  int32_t n_cams;
+  const CamDev* cams;
+  const int32_t* tile_start;  // [n_cams + 1] prefix sums of tiles
+  int32_t total_tiles;
+  int32_t tile_w, tile_h, tiles_per_grab;
+  QueueBlock* q;
+};
+
+// Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is double.
+cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s);
+// Largest resident blocks per SM for the kernel of (prec, f64) at this block size.
+cudaError_t batch_occupancy(int prec, bool f64, int block, int* blocks_per_sm);
+// Registers per thread of that kernel (for stats).
+int batch_regs(int prec, bool f64);
+
+}  // namespace amr

@@ -1,0 +1,60 @@
+"""The C ABI: every declared symbol is exported, and calls fail cleanly without a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1210_8014_gb300 import _build
+
+ROOT = Path(__file__).resolve().parents[1]
+DECL = re.compile(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*\**\s*([a-z_][a-z0-9_]*)\s*\(", re.M)
+
+
+def declared(header: Path):
+    text = re.sub(r"/\*.*?\*/", "", header.read_text(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    names = set(DECL.findall(text))
+    return sorted(n for n in names if not n.startswith("defined"))
+
+
+LIBS = {"amr.h": _build.build_amr, "amr_gen.h": _build.build_gen}
+
+
+@pytest.mark.parametrize("header", sorted(LIBS))
+def test_every_declared_symbol_is_exported(header):
+    names = declared(ROOT / "include" / header)
+    assert len(names) >= 5
+    lib = ctypes.CDLL(str(LIBS[header]()))
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_amr_h_declares_the_boundary():
+    names = set(declared(ROOT / "include" / "amr.h"))
+    for n in ("amr_create", "amr_destroy", "amr_load_octree", "amr_render", "amr_render_batch", "amr_submit",
+              "amr_wait", "amr_stats", "amr_last_error", "amr_autotune"):
+        assert n in names
+
+
+def test_camera_struct_layout_matches_header():
+    from paper_1210_8014_gb300 import amr
+    assert ctypes.sizeof(amr.amr_camera) == 14 * 8 + 10 * 4
+    assert ctypes.sizeof(amr.amr_options) == 6 * 4
+
+
+def test_calls_fail_cleanly_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1210_8014_gb300 import amr
+    with pytest.raises(amr.AmrError) as e:
+        amr.amr_create(0)
+    assert e.value.status in (amr.AMR_E_CUDA, amr.AMR_E_INVALID)
+    assert amr.amr_last_error()
+    # null context / null arguments are rejected before any device work
+    L = amr.lib()
+    assert L.amr_render(None, None, None, None, 1, None) == amr.AMR_E_INVALID
+    assert L.amr_render_batch(None, 1, None, None, None, 1, None) == amr.AMR_E_INVALID
+    assert L.amr_destroy(None) == amr.AMR_OK
+    assert L.amr_stats(None, None, 0) == amr.AMR_E_INVALID

@@ -1,0 +1,299 @@
+"""CUDA path vs the CPU oracle, through the C ABI (pytest -m gpu).
+
+Counts are compared bit-exactly; maps within the tolerances of tests/parity.py
+(FP64 kernel 1e-12, FP32 compensated 1e-5, max mode bit-exact).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import oracle_pins
+from parity import assert_parity, errors
+from paper_1210_8014_gb300 import amr, inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = (amr.AMR_PREC_FP64, amr.AMR_PREC_FP32_KAHAN, amr.AMR_PREC_FP32_PLAIN)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return 0
+
+
+_trees = {}
+
+
+def tree_of(name):
+    if name not in _trees:
+        if name == "tiny":
+            _trees[name] = inputs.plain_tree(np.float64)
+        elif name == "galaxy":
+            _trees[name] = inputs.galaxy_precision_tree(np.float32)
+        elif name == "batch":
+            _trees[name] = inputs.batch_tree(np.float32)
+    return _trees[name]
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_golden_cases_on_gpu(gpu):
+    tree, cases = oracle_pins.golden_tree()
+    with amr.Renderer(tree) as r:
+        for case in cases:
+            for p in PRECS:
+                cam = oracle_pins.golden_camera(case).with_(precision=p)
+                m, c = r.render(cam)
+                torch.cuda.synchronize()
+                assert int(host(c)[0, 0]) == case["count"], (case["name"], p)
+                tol = 1e-15 if p == 0 else 1e-6
+                got = float(host(m)[0, 0])
+                assert abs(got - case["expected"]) <= tol * max(1.0, abs(case["expected"])), (case["name"], p, got)
+
+
+def test_tiny_plain_method_fp64_and_fp32(gpu):
+    tree = tree_of("tiny")
+    cam = inputs.tiny_workload()[1][0]
+    ref, rc = oracle.render(tree, cam)
+    with amr.Renderer(tree) as r:
+        for p in PRECS:
+            m, c = r.render(cam.with_(precision=p))
+            e = assert_parity(0, p, host(m), host(c), ref, rc, field_is_f32=False, ctx=f"tiny prec {p}")
+            if p == 0:
+                assert e["max"] <= 1e-12
+
+
+@pytest.mark.parametrize("k", range(len(oracle_pins._bruteforce_cases())))
+def test_random_small_trees_all_modes(gpu, k):
+    tree, cam = oracle_pins._bruteforce_cases()[k]
+    ref, rc = oracle.render(tree, cam)
+    with amr.Renderer(tree) as r:
+        for p in PRECS:
+            m, c = r.render(cam.with_(precision=p))
+            assert_parity(cam.mode, p, host(m), host(c), ref, rc, field_is_f32=False, ctx=f"case {k} prec {p}")
+
+
+def ragged_cameras(tree, n=(203, 157)):
+    rng = np.random.default_rng(2)
+    w = inputs.random_direction(rng)
+    return [inputs.camera_along(w, fov=1.0, n=n, max_level=tree.depth, mode=m) for m in (0, 1, 2)]
+
+
+def test_galaxy_full_map_every_mode_and_precision(gpu):
+    tree = tree_of("galaxy")
+    with amr.Renderer(tree) as r:
+        for cam in ragged_cameras(tree):
+            ref, rc = oracle.render(tree, cam)
+            for p in PRECS:
+                m, c = r.render(cam.with_(precision=p))
+                assert_parity(cam.mode, p, host(m), host(c), ref, rc, ctx=f"galaxy mode {cam.mode} prec {p}")
+
+
+def test_galaxy_1024_sampled_pixels(gpu):
+    """The 1024^2 precision workload at full size, checked on sampled pixels."""
+    tree = tree_of("galaxy")
+    cams = inputs.galaxy_precision_cameras(tree)
+    rng = np.random.default_rng(0)
+    pi = rng.integers(0, 1024, 3000)
+    pj = rng.integers(0, 1024, 3000)
+    with amr.Renderer(tree) as r:
+        refs = {}
+        for cam in cams:
+            if cam.mode not in refs:
+                refs[cam.mode] = oracle.render(tree, cam, pixels=(pi, pj))
+            ref, rc = refs[cam.mode]
+            m, c = r.render(cam)
+            assert_parity(cam.mode, cam.precision, host(m)[pj, pi], host(c)[pj, pi], ref, rc,
+                          ctx=f"1024 mode {cam.mode} prec {cam.precision}")
+
+
+def test_kahan_beats_plain_fp32(gpu):
+    tree = tree_of("galaxy")
+    cam = inputs.galaxy_precision_cameras(tree, n=256)[0]
+    ref, _ = oracle.render(tree, cam)
+    with amr.Renderer(tree) as r:
+        mk, _ = r.render(cam.with_(precision=amr.AMR_PREC_FP32_KAHAN))
+        mp, _ = r.render(cam.with_(precision=amr.AMR_PREC_FP32_PLAIN))
+        ek = errors(0, host(mk), ref)
+        ep = errors(0, host(mp), ref)
+    assert ek["max"] <= 1e-5
+    assert ek["p99"] <= ep["p99"], (ek, ep)
+
+
+def mixed_batch(tree, n_cams, seed, sizes=((128, 128), (130, 77), (256, 256), (33, 5), (512, 300))):
+    rng = np.random.default_rng(seed)
+    normal = tree.info.get("normal", (0, 0, 1))
+    cams = []
+    for q in range(n_cams):
+        nx, ny = sizes[q % len(sizes)]
+        cams.append(inputs.camera_along(inputs.random_direction(rng), centre=inputs.disk_point(rng, normal),
+                                        fov=float(2.0 ** rng.uniform(-6, 0)), n=(nx, ny), max_level=-1,
+                                        mode=int(rng.integers(0, 3)), precision=int(rng.integers(0, 3))))
+    return cams
+
+
+def test_batch_equals_alone_and_oracle(gpu):
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 20, seed=7)
+    with amr.Renderer(tree) as r:
+        outs = r.render_batch(cams)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(1)
+        for q, cam in enumerate(cams):
+            m1, c1 = r.render(cam)
+            assert torch.equal(outs[q][0], m1) and torch.equal(outs[q][1], c1), f"camera {q}: batch != alone"
+            pi = rng.integers(0, cam.nx, 64)
+            pj = rng.integers(0, cam.ny, 64)
+            ref, rc = oracle.render(tree, cam, pixels=(pi, pj))
+            assert_parity(cam.mode, cam.precision, host(m1)[pj, pi], host(c1)[pj, pi], ref, rc, ctx=f"cam {q}")
+
+
+def test_segments_counter_matches_counts(gpu):
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 8, seed=3)
+    with amr.Renderer(tree) as r:
+        before = r.stats()["segments"]
+        outs = r.render_batch(cams)
+        torch.cuda.synchronize()
+        total = sum(int(o[1].sum()) for o in outs)
+        # stats harvest completed launches
+        after = r.stats()["segments"]
+        assert after - before == total
+
+
+def test_host_output_path(gpu):
+    tree = tree_of("galaxy")
+    cam = ragged_cameras(tree, n=(64, 48))[0].with_(precision=amr.AMR_PREC_FP32_KAHAN)
+    with amr.Renderer(tree) as r:
+        md, cd = r.render(cam)
+        mh = np.zeros((48, 64), np.float32)
+        ch = np.zeros((48, 64), np.int32)
+        amr.amr_render(r.ctx, cam, mh, ch, 0)
+        assert (mh == host(md)).all() and (ch == host(cd)).all()
+        mb = [np.zeros((48, 64), np.float32), np.zeros((48, 64), np.float64)]
+        cams = [cam, cam.with_(precision=0, mode=1)]
+        amr.amr_render_batch(r.ctx, cams, mb, None, 0)
+        m2, _ = r.render(cams[1])
+        assert (mb[0] == host(md)).all() and (mb[1] == host(m2)).all()
+
+
+def test_deterministic(gpu):
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 6, seed=11)
+    with amr.Renderer(tree) as r:
+        a = r.render_batch(cams)
+        b = r.render_batch(cams)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
+
+
+def test_edge_cases(gpu):
+    tree = oracle_pins.golden_tree()[0]
+    outside = inputs.Camera((-0.5, 0.5, 0.5), (0, 0, 1), (1, 0, 0), (0, 1, 0), (0.2, 0.2), 7, 3, max_level=2)
+    cams = [
+        inputs.camera_along((0.2, 0.3, 0.9), n=1, max_level=2),             # single pixel
+        inputs.camera_along((0.2, 0.3, 0.9), n=(33, 5), max_level=9),       # ragged, level clamped to depth
+        inputs.camera_along((0.0, -1.0, 0.0), n=(17, 31), max_level=1),     # level 1, axis-aligned
+        outside,                                                             # misses the box: zeros
+        inputs.camera_along((1.0, 1.0, 1.0), fov=1.8, n=(40, 40), max_level=2),
+    ]
+    with amr.Renderer(tree) as r:
+        for k, cam in enumerate(cams):
+            for mode in (0, 1, 2):
+                for p in PRECS:
+                    c2 = cam.with_(mode=mode, precision=p)
+                    ref, rc = oracle.render(tree, c2)
+                    m, c = r.render(c2)
+                    assert_parity(mode, p, host(m), host(c), ref, rc, field_is_f32=False, ctx=f"edge {k}")
+        m, c = r.render(outside)
+        assert int(c.sum()) == 0 and float(m.abs().sum()) == 0.0
+        assert amr.amr_camera_check(r.ctx, cams[1]) == 2
+
+
+def test_invalid_cameras_rejected(gpu):
+    tree = oracle_pins.golden_tree()[0]
+    base = inputs.camera_along((0, 0, 1), n=8, max_level=2)
+    bad = [base.with_(nx=0), base.with_(mode=5), base.with_(precision=9), base.with_(u=(1.0, 0.1, 0.0)),
+           base.with_(fov=(0.0, 1.0)), base.with_(centre=(5.0, 0.5, 0.5)), base.with_(field_value=7),
+           base.with_(mode=1, field_vel=(1, 2, 9)), base.with_(max_level=0), base.with_(centre=(float("nan"), 0.5, 0.5))]
+    with amr.Renderer(tree) as r:
+        for k, cam in enumerate(bad):
+            with pytest.raises(amr.AmrError) as e:
+                r.render(cam)
+            assert e.value.status == amr.AMR_E_INVALID, k
+
+
+def test_bad_trees_rejected(gpu):
+    tree, _ = oracle_pins.golden_tree()
+    ctx = amr.amr_create(0)
+    try:
+        def load(level, coord, child):
+            f = [np.zeros((len(level), 8))]
+            amr.amr_load_octree(ctx, len(level), np.array(level, np.uint8), np.array(coord, np.int32),
+                                np.array(child, np.int32), f, amr.AMR_F64)
+
+        ok = (tree.level, tree.coord, tree.child)
+        load(*ok)
+        cases = {
+            "root level": ([2, 2], tree.coord, tree.child),
+            "child level": ([1, 3], tree.coord, tree.child),
+            "child coord": (tree.level, [[0, 0, 0], [2, 0, 0]], tree.child),
+            "shared child": ([1, 2], tree.coord, [[1, 1, -1, -1, -1, -1, -1, -1], [-1] * 8]),
+            "cycle": ([1, 2], tree.coord, [[1] + [-1] * 7, [1] + [-1] * 7]),
+            "unreachable": ([1, 2], tree.coord, [[-1] * 8, [-1] * 8]),
+            "index range": ([1, 2], tree.coord, [[5] + [-1] * 7, [-1] * 8]),
+            "odd coord": ([1, 2], [[0, 0, 0], [1, 0, 0]], tree.child),
+        }
+        for name, (lv, co, ch) in cases.items():
+            with pytest.raises(amr.AmrError) as e:
+                load(lv, co, ch)
+            assert e.value.status == amr.AMR_E_BADTREE, name
+            assert "oct" in str(e.value), name
+    finally:
+        amr.amr_destroy(ctx)
+
+
+def test_autotune_keeps_results(gpu):
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 10, seed=5)
+    with amr.Renderer(tree) as r:
+        a = r.render_batch(cams)
+        best, ms = amr.amr_autotune(r.ctx, cams, reps=1)
+        assert best["tile_w"] * best["tile_h"] == 32 and ms > 0
+        b = r.render_batch(cams)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
+
+
+def test_server_alone_vs_mix(gpu):
+    """Requests submitted together overlap on the device; each result equals
+    the same camera rendered alone."""
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 24, seed=9)
+    with amr.Renderer(tree) as r:
+        amr.amr_server_config(r.ctx, slots=3, map_budget_bytes=8 << 20, max_batch=6)
+        bufs, tickets = [], []
+        for cam in cams:
+            mh = np.zeros((cam.ny, cam.nx), np.float64 if cam.precision == 0 else np.float32)
+            ch = np.zeros((cam.ny, cam.nx), np.int32)
+            bufs.append((mh, ch))
+            tickets.append(amr.amr_submit(r.ctx, cam, mh, ch))
+        for t in tickets:
+            amr.amr_wait(r.ctx, t, 60_000_000)
+        for cam, (mh, ch) in zip(cams, bufs):
+            m1, c1 = r.render(cam)
+            assert (mh == host(m1)).all() and (ch == host(c1)).all()
+        st = r.stats()["server"]
+        assert st["done"] == len(cams) and st["failed"] == 0
+        assert st["p99_ms"] >= st["p50_ms"] > 0
+        with pytest.raises(amr.AmrError) as e:
+            amr.amr_wait(r.ctx, 10 ** 9, 0)
+        assert e.value.status == amr.AMR_E_INVALID
