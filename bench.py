@@ -1,0 +1,387 @@
+"""Benchmark: Gsegments/s of the octree ray-casting pass on one GB300.
+
+A step is one pass of the whole hot path over one batch: 64 cameras of uneven
+map sizes (128^2 .. 2048^2), fields of view (1 .. 1/64 of the box) and level
+cuts, mixed modes (column / weighted mean / max), rendered by one persistent
+launch fed by the ray-tile work queue, on a ~16M-leaf synthetic galaxy octree
+(levels 7-12 reached, cap 16, density + 3 velocity fields, float32), FP32
+compensated accumulation.  A segment is one leaf crossed by one ray (the sum
+of the per-pixel visited counts).  The same batch is also timed with the FP64
+kernel, and the FP32 maps are compared with the FP64 ones.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config batch|precision|zoom]
+
+--impl reference times the CPU oracle (plain FP64 C, all host cores) on a
+bounded sample of each step's rays.  Under torchrun (N > 1) every rank renders
+its own batch (seeded by rank, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Gsegments/s (FP32-Kahan batch; FP64 kernel and rel err vs FP64 reported beside)"
+UNIT = "Gsegments/s"
+BYTES_PER_SEG = {0: 8, 1: 20, 2: 8}   # child word + scalars per segment, float32 fields
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--config", choices=("batch", "precision", "zoom"), default="batch")
+    ap.add_argument("--cams", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(config, rank, n_cams, precision):
+    from paper_1210_8014_gb300 import inputs
+    if config == "batch":
+        tree = inputs.batch_tree()
+        cams = inputs.batch_cameras(tree, n_cams=n_cams, precision=precision, seed=3 + 1000 * rank)
+        name = (f"{n_cams}-camera batch, sizes 128^2..2048^2, fov 1..1/64, pixel-rule level cut, mixed modes; "
+                f"galaxy octree {tree.n_leaves} leaves (levels {min(map(int, tree.info['leaf_hist']))}-{tree.depth}, "
+                f"mass threshold 2^-22 of total)")
+    elif config == "precision":
+        tree = inputs.galaxy_precision_tree()
+        cams = [c for c in inputs.galaxy_precision_cameras(tree, precisions=(precision,))]
+        name = f"1024^2 random-direction view, 3 modes; galaxy octree {tree.n_leaves} leaves, threshold 2^-20"
+    else:
+        tree = inputs.zoom_tree()
+        cams = inputs.zoom_cameras(tree, precision=precision)
+        name = f"8-frame 4096^2 zoom toward the centre; galaxy octree {tree.n_leaves} leaves to level {tree.depth}"
+    return tree, cams, name
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_1210_8014_gb300" / "csrc" / "amr").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(config):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    f = ROOT / "profiles" / f"batch_kernel_{config}_traffic.txt"
+    if not f.exists():
+        return None
+    kv = {}
+    for line in f.read_text().splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
+    """The oracle as it stands, on a bounded random sample of the batch's rays."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    threads = os.cpu_count() or 1
+    lib = oracle.load()
+    per_cam = 8
+    total_segs, total_t, total_rays = 0, 0.0, 0
+    while True:
+        for cam in cams:
+            pi = rng.integers(0, cam.nx, per_cam)
+            pj = rng.integers(0, cam.ny, per_cam)
+            t0 = time.perf_counter()
+            _, cnt = oracle.render(tree, cam, pixels=(pi, pj), threads=threads, lib=lib)
+            total_t += time.perf_counter() - t0
+            total_segs += int(cnt.sum())
+            total_rays += per_cam
+        if total_t >= budget_s or per_cam >= 4096:
+            break
+        per_cam = int(min(4096, per_cam * max(2.0, budget_s / max(total_t, 1e-3) * 0.6)))
+    return {"value": total_segs / total_t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{total_rays} random rays spread over the {len(cams)} cameras "
+                      f"({total_segs} segments, {total_t:.1f} s of oracle time)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    from paper_1210_8014_gb300 import inputs
+    import oracle
+    tree, cams, name = workload(args.config, 0, args.cams, inputs.PREC_FP32_KAHAN)
+    lib = oracle.load()
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(123)
+    per_cam = 32 if args.config == "batch" else 512
+
+    def step():
+        segs = 0
+        t0 = time.perf_counter()
+        for cam in cams:
+            pi = rng.integers(0, cam.nx, per_cam)
+            pj = rng.integers(0, cam.ny, per_cam)
+            _, cnt = oracle.render(tree, cam, pixels=(pi, pj), threads=threads, lib=lib)
+            segs += int(cnt.sum())
+        return segs, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    tot_s, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        s, t = step()
+        tot_s += s
+        tot_t += t
+    value = tot_s / tot_t / 1e9
+    sample = f"{per_cam} random rays per camera per step ({per_cam * len(cams)} rays/step)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+int128",
+        "data": "synthetic", "config": {"workload": name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = local if world > 1 else 0
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+
+    t0 = time.perf_counter()
+    tree, cams32, name = workload(args.config, rank, args.cams, inputs.PREC_FP32_KAHAN)
+    cams64 = [c.with_(precision=inputs.PREC_FP64) for c in cams32]
+    gen_s = time.perf_counter() - t0
+    r = amr.Renderer(tree, device=device)
+    t1 = time.perf_counter()
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t1
+    stream = torch.cuda.Stream(device=device)
+    tuned = None
+    if args.autotune:
+        tuned, _ = amr.amr_autotune(r.ctx, cams32, reps=1)
+
+    def outputs(cams):
+        maps = [torch.empty((c.ny, c.nx), dtype=torch.float64 if c.precision == 0 else torch.float32, device=dev)
+                for c in cams]
+        cnts = [torch.empty((c.ny, c.nx), dtype=torch.int32, device=dev) for c in cams]
+        return maps, cnts
+
+    m32, c32 = outputs(cams32)
+    m64, c64 = outputs(cams64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def launch(cams, maps, cnts):
+        amr.amr_render_batch(r.ctx, cams, maps, cnts, 1, stream.cuda_stream)
+
+    # warm-up, parity of FP32 vs FP64 on this batch, per-camera segments
+    for _ in range(max(1, args.warmup)):
+        launch(cams32, m32, c32)
+        launch(cams64, m64, c64)
+    torch.cuda.synchronize()
+    seg_cam = [int(c.sum()) for c in c32]
+    assert seg_cam == [int(c.sum()) for c in c64], "FP32 and FP64 kernels visited different leaves"
+    segs = sum(seg_cam)
+    algo_bytes = sum(s * BYTES_PER_SEG[c.mode] for s, c in zip(seg_cam, cams32))
+    err = {"column": 0.0, "wmean": 0.0, "max": 0.0}
+    for c, a, b in zip(cams32, m32, m64):
+        a = a.double()
+        if c.mode == 0:
+            pos = b > 0
+            e = float(((a[pos] - b[pos]).abs() / b[pos]).max()) if bool(pos.any()) else 0.0
+            err["column"] = max(err["column"], e)
+        elif c.mode == 1:
+            s = float(b.abs().max())
+            err["wmean"] = max(err["wmean"], float((a - b).abs().max()) / s if s > 0 else 0.0)
+        else:
+            err["max"] = max(err["max"], float((a - b).abs().max()))
+
+    def timed(cams, maps, cnts, steps):
+        times = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch(cams, maps, cnts)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - wall0
+        return times, wall
+
+    with Clocks(device) as clk:
+        t32, wall32 = timed(cams32, m32, c32, args.steps)
+    t64, _ = timed(cams64, m64, c64, max(3, args.steps // 2))
+    ms32 = float(np.mean(t32))
+    ms64 = float(np.mean(t64))
+    if world > 1:
+        x = torch.tensor([ms32], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        ms32 = float(x.item())
+    value = world * segs / (ms32 * 1e-3) / 1e9
+    value64 = segs / (ms64 * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: camera upload and map/count readback inside
+    hmaps = [np.empty((c.ny, c.nx), np.float32) for c in cams32]
+    hcnts = [np.empty((c.ny, c.nx), np.int32) for c in cams32]
+    amr.amr_render_batch(r.ctx, cams32, hmaps, hcnts, 0)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        amr.amr_render_batch(r.ctx, cams32, hmaps, hcnts, 0)
+        e2e_t.append(time.perf_counter() - a)
+    e2e_ms = float(np.mean(e2e_t)) * 1e3
+    d2h = sum(m.nbytes + c.nbytes for m, c in zip(hmaps, hcnts))
+    h2d = len(cams32) * 152
+
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (ms32 * 1e-3) / 1e9
+    stats = r.stats()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
+        "config": {"workload": name, "cameras": len(cams32), "rays_per_step": int(sum(c.nx * c.ny for c in cams32)),
+                   "segments_per_step": segs, "l2": "256 MiB buffer written between timed steps",
+                   "options": tuned or amr.amr_get_options(r.ctx).as_dict(), "parallelism": f"replicas{world}"},
+        "ms_per_frame": ms32 / len(cams32),
+        "fp64_kernel": {"value": value64, "ms_per_step": ms64, "unit": UNIT},
+        "fp32_over_fp64": value / world / value64,
+        "fp32_vs_fp64_err": err,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(args.config), "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "e2e": {"value": segs / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "timed_wall_s": wall32,
+        "setup_s": {"generate": gen_s, "load": load_s},
+        "regs": stats.get("regs"),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(tree, cams32)
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

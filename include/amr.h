@@ -121,7 +121,7 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
  * Render one camera.  map_out: nx*ny values, double for AMR_PREC_FP64 and float
  * otherwise, row-major [ny][nx].  count_out (nullable): nx*ny int32 visited-leaf
  * counts.  out_on_device != 0: both are device pointers and the call returns once
- * the work is enqueued on `cuda_stream` (a cudaStream_t; NULL = the context's own
+ * the work is enqueued on `cuda_stream` (a cudaStream_t; NULL = the CUDA default
  * stream); out_on_device == 0: host pointers, and the call returns when the
  * results are in them.
  */

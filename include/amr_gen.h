@@ -38,7 +38,7 @@ typedef struct amrgen_tree amrgen_tree;
 
 enum {
   AMRGEN_PLAIN = 0,   /* rho = 1 + 100 exp(-|x-c|^2 / (2*0.05^2)), absolute mass threshold */
-  AMRGEN_GALAXY = 1   /* exponential disk x lognormal random field (+ optional Plummer clumps) */
+  AMRGEN_GALAXY = 1   /* 1e-6 background + exponential disk x lognormal random field (+ optional Plummer clumps) */
 };
 
 typedef struct {

@@ -427,7 +427,7 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
     stage_bytes += ((map_bytes(cams[i]) + 255) / 256) * 256;
     if (counts && counts[i]) stage_bytes += ((px * 4 + 255) / 256) * 256;
   }
-  cudaStream_t stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;  // NULL: the CUDA default stream
   if (out_on_device) {
     for (int i = 0; i < n; ++i) {
       dev[i].map = maps[i];

@@ -7,7 +7,7 @@
 // fields and the refinement rule are readings written down with the workloads:
 //   plain  : rho = 1 + 100 exp(-|x-c|^2 / (2*0.05^2)), refine while
 //            rho(centre) 8^-l > threshold.
-//   galaxy : rho = exp(-R/0.05) exp(-|z|/0.005) exp(0.5 g) in a disk frame
+//   galaxy : rho = 1e-6 + exp(-R/0.05) exp(-|z|/0.005) exp(0.5 g) in a disk frame
 //            with a seeded normal, g a unit-variance Gaussian random field with
 //            P(k) ~ k^-11/3 made of seeded Fourier modes; refine while
 //            rho(centre) 8^-l > threshold * (total mass of the base grid).
@@ -27,6 +27,10 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxLevel = 22;
+// Uniform background density of the galaxy model (1e-6 of the central disk
+// density): keeps every float32 density and column far above the float32
+// underflow range; the bare exponential disk falls below 1e-38 at |z| ~ 0.44.
+constexpr double kBackground = 1e-6;
 
 // splitmix64: a published counter-based mixer (Steele, Lea, Flood 2014).
 struct Rng {
@@ -192,7 +196,7 @@ struct Model {
     double zz = d[0] * normal[0] + d[1] * normal[1] + d[2] * normal[2];
     double pr[3] = {d[0] - zz * normal[0], d[1] - zz * normal[1], d[2] - zz * normal[2]};
     double R = std::sqrt(pr[0] * pr[0] + pr[1] * pr[1] + pr[2] * pr[2]);
-    return std::exp(-R / 0.05) * std::exp(-std::fabs(zz) / 0.005) * std::exp(0.5 * gval);
+    return kBackground + std::exp(-R / 0.05) * std::exp(-std::fabs(zz) / 0.005) * std::exp(0.5 * gval);
   }
 
   double clump_density(const double x[3]) const {
