@@ -169,6 +169,39 @@ amr_status amr_submit(amr_ctx* ctx, const amr_camera* cam, void* map, int32_t* c
 amr_status amr_wait(amr_ctx* ctx, uint64_t ticket, int64_t timeout_us);
 amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket);
 
+/*
+ * amr_render_batch without any GPU allocation.  The paper has no counterpart:
+ * this is for callers that cannot call cudaMalloc, such as a renderer living
+ * inside a simulation whose memory manager owns the whole GPU (in-situ
+ * visualisation), a latency-critical loop where an allocation could stall on a
+ * device-wide synchronisation, or a process held to a fixed memory footprint.
+ * It needs no context: the caller passes the tree, the cameras and the outputs,
+ * and the launch scratch (camera table, tile prefix sums, work-queue head) lives
+ * in a fixed library-owned device array of under 96 KiB that every GPU loading
+ * this library holds until exit.
+ *   records   device, [n_oct] uint64: bits 0-31 index of the oct's first child
+ *             oct, bits 32-39 its refinement mask (bit c set: cell c refined).
+ *             Octs breadth-first from the root (index 0, level 1), the children
+ *             of an oct contiguous in cell order (the layout amr_load_octree
+ *             builds; a breadth-first tree whose siblings are adjacent maps 1:1).
+ *   depth     deepest oct level in the tree (1..22).
+ *   fields    host array of n_fields device pointers, each [n_oct][8] values of
+ *             field_dtype, in the same oct order.
+ *   cams, maps, counts, cuda_stream: as in amr_render_batch with device outputs.
+ * At most AMR_NOALLOC_MAX_CAMERAS cameras per call; more is AMR_E_INVALID.
+ * Runs on the calling thread's current device and returns once enqueued.  The
+ * first call on a device looks up the scratch's device address; make that first
+ * call before any stream capture.  All calls share the scratch and clear its
+ * queue at the start: calls that overlap on the GPU race on it, so order them
+ * on one stream.  Record contents are not validated on the host; a child index
+ * at or beyond n_oct ends that ray instead of being read.
+ */
+#define AMR_NOALLOC_MAX_CAMERAS 256
+amr_status amr_render_batch_noalloc(int64_t n_oct, const uint64_t* records, int32_t depth, int32_t n_fields,
+                                    const void* const* fields, int32_t field_dtype, int32_t n,
+                                    const amr_camera* cams, void* const* maps, int32_t* const* counts,
+                                    void* cuda_stream);
+
 /* JSON counters: renders, rays, segments, tree bytes, options, server latency. */
 amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len);
 

@@ -79,6 +79,8 @@ def lib():
             "amr_cancel": [P, ctypes.c_uint64],
             "amr_stats": [P, ctypes.c_char_p, I64],
             "amr_tree_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)],
+            "amr_render_batch_noalloc": [I64, P, I32, I32, ctypes.POINTER(P), I32, I32, ctypes.POINTER(amr_camera),
+                                         ctypes.POINTER(P), ctypes.POINTER(P), P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -212,6 +214,22 @@ def amr_tree_info(ctx):
     n, d, b = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
     _check(lib().amr_tree_info(ctx, ctypes.byref(n), ctypes.byref(d), ctypes.byref(b)))
     return int(n.value), int(d.value), int(b.value)
+
+
+AMR_NOALLOC_MAX_CAMERAS = 256
+
+
+def amr_render_batch_noalloc(n_oct: int, records, depth: int, fields: Sequence, field_dtype: int,
+                             cams: Sequence[Camera], maps: Sequence, counts: Optional[Sequence] = None,
+                             cuda_stream=None) -> None:
+    """Batch render with no GPU allocation: tree, maps and counts are the caller's device buffers."""
+    n = len(cams)
+    farr = (ctypes.c_void_p * len(fields))(*[_ptr(f) for f in fields])
+    carr = (amr_camera * max(n, 1))(*[to_camera(c) for c in cams])
+    marr = (ctypes.c_void_p * max(n, 1))(*[_ptr(m) for m in maps])
+    karr = (ctypes.c_void_p * max(n, 1))(*[_ptr(k) for k in counts]) if counts is not None else None
+    _check(lib().amr_render_batch_noalloc(int(n_oct), _ptr(records), int(depth), len(fields), farr, int(field_dtype),
+                                          n, carr, marr, karr, _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 # ---------------------------------------------------------------- convenience

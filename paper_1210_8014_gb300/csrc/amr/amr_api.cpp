@@ -209,15 +209,14 @@ void pixel_centre(const amr_camera& c, int i, int j, double x[3]) {
 
 // Camera -> the constants its rays need (Sec. 2: the camera fixes the deepest
 // level read).  Returns AMR_E_INVALID with a message on a bad camera.
-amr_status canonicalise(const amr_ctx* ctx, const amr_camera& c, int tile_w, int tile_h, CamDev& d) {
-  const DeviceTree& t = ctx->tree;
-  if (!t.rec) return fail(AMR_E_INVALID, "no octree loaded");
+amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int tile_w, CamDev& d) {
+  if (!t.loaded) return fail(AMR_E_INVALID, "no octree loaded");
   if (c.nx <= 0 || c.ny <= 0 || (int64_t)c.nx * c.ny >= (int64_t(1) << 31))
     return fail(AMR_E_INVALID, "map size %d x %d out of range", c.nx, c.ny);
   if (c.mode < AMR_MODE_COLUMN || c.mode > AMR_MODE_MAX) return fail(AMR_E_INVALID, "unknown mode %d", c.mode);
   if (c.precision < AMR_PREC_FP64 || c.precision > AMR_PREC_FP32_PLAIN)
     return fail(AMR_E_INVALID, "unknown precision %d", c.precision);
-  const int nf = (int)t.fields.size();
+  const int nf = t.n_fields;
   auto fok = [nf](int f) { return f >= 0 && f < nf; };
   if (c.mode == AMR_MODE_WMEAN) {
     if (!fok(c.field_weight) || !fok(c.field_vel[0]) || !fok(c.field_vel[1]) || !fok(c.field_vel[2]))
@@ -292,8 +291,14 @@ amr_status canonicalise(const amr_ctx* ctx, const amr_camera& c, int tile_w, int
   } else {
     d.rho = t.fields[c.field_value];
   }
-  (void)tile_h;
   return AMR_OK;
+}
+
+amr_status canonicalise(const amr_ctx* ctx, const amr_camera& c, int tile_w, int tile_h, CamDev& d) {
+  (void)tile_h;
+  const DeviceTree& t = ctx->tree;
+  const amr::TreeView view{t.fields.data(), (int)t.fields.size(), t.depth, t.rec != nullptr};
+  return canonicalise_tree(view, c, tile_w, d);
 }
 
 int64_t tiles_of(const CamDev& d, int tile_w, int tile_h) {
@@ -632,6 +637,16 @@ void free_tree(DeviceTree& t) {
 }
 
 }  // namespace
+
+namespace amr {
+
+amr_status canonicalise_view(const TreeView& t, const amr_camera& c, int tile_w, CamDev& d) {
+  return canonicalise_tree(t, c, tile_w, d);
+}
+
+amr_status set_error(amr_status st, const char* msg) { return fail(st, "%s", msg); }
+
+}  // namespace amr
 
 extern "C" {
 

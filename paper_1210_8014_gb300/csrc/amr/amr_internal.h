@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "amr.h"
+
 namespace amr {
 
 constexpr int kFixBits = 36;      // fixed-point bits of a coordinate: level 22 + 14 guard bits
@@ -52,6 +54,20 @@ struct BatchArgs {
   int32_t tile_w, tile_h, tiles_per_grab;
   QueueBlock* q;
 };
+
+// The loaded tree as camera canonicalisation needs it.
+struct TreeView {
+  const void* const* fields;  // device pointers, one per field
+  int n_fields;
+  int depth;                  // deepest oct level present
+  bool loaded;
+};
+
+// Camera -> CamDev (tile_w: pixels per tile row).  On failure returns
+// AMR_E_INVALID and sets the calling thread's amr_last_error() message.
+int32_t canonicalise_view(const TreeView& t, const amr_camera& c, int tile_w, CamDev& d);
+// Set the calling thread's amr_last_error() message; returns st.
+int32_t set_error(int32_t st, const char* msg);
 
 // Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is double.
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s);
