@@ -172,6 +172,7 @@ def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
     rng = np.random.default_rng(seed)
     threads = os.cpu_count() or 1
     lib = oracle.load()
+    tree = oracle.prepare(tree)
     per_cam = 8
     total_segs, total_t, total_rays = 0, 0.0, 0
     while True:
@@ -183,9 +184,9 @@ def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
             total_t += time.perf_counter() - t0
             total_segs += int(cnt.sum())
             total_rays += per_cam
-        if total_t >= budget_s or per_cam >= 4096:
+        if total_t >= budget_s or per_cam >= 65536:
             break
-        per_cam = int(min(4096, per_cam * max(2.0, budget_s / max(total_t, 1e-3) * 0.6)))
+        per_cam = int(min(65536, per_cam * max(2.0, budget_s / max(total_t, 1e-3) * 0.6)))
     return {"value": total_segs / total_t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{total_rays} random rays spread over the {len(cams)} cameras "
                       f"({total_segs} segments, {total_t:.1f} s of oracle time)"}
@@ -199,6 +200,7 @@ def run_reference(args):
     import oracle
     tree, cams, name = workload(args.config, 0, args.cams, inputs.PREC_FP32_KAHAN)
     lib = oracle.load()
+    tree = oracle.prepare(tree)
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(123)
     per_cam = 32 if args.config == "batch" else 512

@@ -86,18 +86,31 @@ def to_camera(cam) -> OracleCamera:
     return c
 
 
+class Prepared:
+    """The oracle's view of a tree: contiguous arrays, fields widened to float64
+    once (exact for float32 input), so repeated renders pay no conversion."""
+
+    def __init__(self, tree):
+        self.level = np.ascontiguousarray(tree.level, np.uint8)
+        self.coord = np.ascontiguousarray(tree.coord, np.int32)
+        self.child = np.ascontiguousarray(tree.child, np.int32)
+        self.fields = [np.ascontiguousarray(f, np.float64) for f in tree.fields]
+        self.ptrs = (ctypes.c_void_p * len(self.fields))(*[f.ctypes.data for f in self.fields])
+
+
+def prepare(tree) -> Prepared:
+    return tree if isinstance(tree, Prepared) else Prepared(tree)
+
+
 def render(tree, cam, pixels=None, threads: int = 0, lib=None):
     """FP64 map and per-pixel leaf counts.
 
-    pixels: None for the whole [ny, nx] map, else (i_array, j_array) and the
-    results are 1-D in that order.
+    tree: an input tree or a Prepared one.  pixels: None for the whole [ny, nx]
+    map, else (i_array, j_array) and the results are 1-D in that order.
     """
     lib = lib or load()
-    level = np.ascontiguousarray(tree.level, np.uint8)
-    coord = np.ascontiguousarray(tree.coord, np.int32)
-    child = np.ascontiguousarray(tree.child, np.int32)
-    f64 = [np.ascontiguousarray(f, np.float64) for f in tree.fields]
-    ptrs = (ctypes.c_void_p * len(f64))(*[f.ctypes.data for f in f64])
+    t = prepare(tree)
+    level, coord, child, f64, ptrs = t.level, t.coord, t.child, t.fields, t.ptrs
     c = to_camera(cam)
     if pixels is None:
         n_pix, pi, pj = -1, None, None

@@ -47,6 +47,7 @@ amr_status fail(amr_status st, const char* fmt, ...) {
 
 struct DeviceTree {
   uint2* rec = nullptr;
+  int32_t* nbr = nullptr;  // [n_oct][6] face-neighbour links
   std::vector<void*> fields;
   int64_t n_oct = 0;
   int depth = 0;
@@ -362,6 +363,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     if (!groups[g] || !tiles_total[g]) continue;
     amr::BatchArgs a{};
     a.rec = ctx->tree.rec;
+    a.nbr = ctx->tree.nbr;
     a.n_oct = (uint32_t)ctx->tree.n_oct;
     a.n_cams = groups[g];
     a.cams = s.d_cams + gstart[g];
@@ -373,7 +375,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     a.q = s.d_q + g;
     int bps = opt.blocks_per_sm;
     if (bps <= 0) {
-      CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, opt.block_threads, &bps));
+      CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, true, opt.block_threads, &bps));
       bps = std::max(1, bps);
     }
     int64_t grid = (int64_t)ctx->sms * bps;
@@ -625,13 +627,64 @@ amr_status linearise(int64_t n, const uint8_t* level, const int32_t* coord, cons
       mask |= 1u << c;
       if (!have) { base = (uint32_t)seen[ch]; have = true; }
     }
-    rec[p] = uint2{base, mask};
+    rec[p] = uint2{base, mask | ((uint32_t)level[o] << 8)};
   }
   return AMR_OK;
 }
 
+// Face-neighbour links (the "fully threaded tree" of RAMSES, Sec. 1), built in
+// breadth-first order from the parent's links.  For oct p and face f = 2 axis +
+// (side > 0): the oct of the same level across that face (>= 0), -1 outside
+// the box, or -(2 + 8 oct + cell) for the deepest existing cell covering the
+// neighbouring region when no oct of p's level exists there (that cell is a
+// leaf).
+void build_neighbours(const std::vector<uint2>& rec, std::vector<int32_t>& nb) {
+  const int64_t n = (int64_t)rec.size();
+  nb.assign((size_t)n * 6, -1);
+  std::vector<int32_t> parent((size_t)n, -1);
+  std::vector<uint8_t> pcell((size_t)n, 0);
+  for (int64_t p = 0; p < n; ++p) {
+    const uint32_t mask = rec[p].y & 0xffu;
+    uint32_t k = rec[p].x;
+    for (int c = 0; c < 8; ++c)
+      if ((mask >> c) & 1u) {
+        parent[k] = (int32_t)p;
+        pcell[k] = (uint8_t)c;
+        ++k;
+      }
+  }
+  auto child_of = [&](int64_t q, int qc) -> int32_t {
+    const uint32_t mask = rec[q].y & 0xffu;
+    return (int32_t)(rec[q].x + __builtin_popcount(mask & ((1u << qc) - 1u)));
+  };
+  for (int64_t p = 1; p < n; ++p) {
+    const int64_t par = parent[p];
+    const int pc = pcell[p];
+    for (int x = 0; x < 3; ++x)
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * x + side;
+        const int bit = (pc >> x) & 1;
+        int64_t q;
+        if (bit != side) {
+          q = par;  // the neighbouring region lies inside the parent oct
+        } else {
+          const int32_t w = nb[(size_t)par * 6 + f];
+          if (w < 0) {  // outside, or one coarser leaf covers the parent's neighbour too
+            nb[(size_t)p * 6 + f] = w;
+            continue;
+          }
+          q = w;
+        }
+        const int qc = pc ^ (1 << x);
+        if ((rec[q].y >> qc) & 1u) nb[(size_t)p * 6 + f] = child_of(q, qc);
+        else nb[(size_t)p * 6 + f] = -(int32_t)(2 + 8 * q + qc);
+      }
+  }
+}
+
 void free_tree(DeviceTree& t) {
   if (t.rec) cudaFree(t.rec);
+  if (t.nbr) cudaFree(t.nbr);
   for (void* f : t.fields) if (f) cudaFree(f);
   t = DeviceTree{};
 }
@@ -729,6 +782,12 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
     return fail(AMR_E_OOM, "host memory for linearisation");
   }
   if (st != AMR_OK) return st;
+  std::vector<int32_t> nb;
+  try {
+    build_neighbours(rec, nb);
+  } catch (const std::bad_alloc&) {
+    return fail(AMR_E_OOM, "host memory for neighbour links");
+  }
   CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   {
     std::lock_guard<std::mutex> lk(ctx->launch_mu);
@@ -754,7 +813,13 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
       return fail(AMR_E_OOM, "device memory for field %d (%zu bytes)", f, fbytes);
     }
   }
+  if (cudaMalloc((void**)&t.nbr, (size_t)n_oct * 6 * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    free_tree(t);
+    return fail(AMR_E_OOM, "device memory for %lld neighbour links", (long long)n_oct * 6);
+  }
   cudaError_t e = cudaMemcpy(t.rec, rec.data(), (size_t)n_oct * sizeof(uint2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.nbr, nb.data(), (size_t)n_oct * 6 * sizeof(int32_t), cudaMemcpyHostToDevice);
   std::vector<char> buf;
   try {
     buf.resize(fbytes);
@@ -774,7 +839,7 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
   t.n_oct = n_oct;
   t.depth = depth;
   t.f64 = field_dtype == AMR_F64;
-  t.bytes = (int64_t)(n_oct * sizeof(uint2) + n_fields * fbytes);
+  t.bytes = (int64_t)(n_oct * (sizeof(uint2) + 6 * sizeof(int32_t)) + n_fields * fbytes);
   ctx->tree = std::move(t);
   return AMR_OK;
 }
@@ -1000,7 +1065,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
       (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
       (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
-      o.use_graph, ctx->autotune_ms, amr::batch_regs(0, f64), amr::batch_regs(1, f64), amr::batch_regs(2, f64),
+      o.use_graph, ctx->autotune_ms, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
       fps);
   if (len < 0) return fail(AMR_E_INVALID, "stats formatting failed");

@@ -45,7 +45,9 @@ struct QueueBlock {
 };
 
 struct BatchArgs {
-  const uint2* rec;         // oct records {first child, refinement mask}
+  const uint2* rec;         // oct records {first child, refinement mask | level << 8}
+  const int32_t* nbr;       // [n_oct][6] face-neighbour links, or null (then the
+                            // kernel finds neighbours through its ancestor stack)
   uint32_t n_oct;
   int32_t n_cams;
   const CamDev* cams;
@@ -71,9 +73,10 @@ int32_t set_error(int32_t st, const char* msg);
 
 // Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is double.
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s);
-// Largest resident blocks per SM for the kernel of (prec, f64) at this block size.
-cudaError_t batch_occupancy(int prec, bool f64, int block, int* blocks_per_sm);
+// Largest resident blocks per SM for the kernel of (prec, f64, with neighbour
+// links) at this block size.
+cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm);
 // Registers per thread of that kernel (for stats).
-int batch_regs(int prec, bool f64);
+int batch_regs(int prec, bool f64, bool nb);
 
 }  // namespace amr

@@ -64,7 +64,7 @@ struct RayOut {
   int count;
 };
 
-template <int PREC, int MODE, typename F>
+template <int PREC, int MODE, bool NB, typename F>
 __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& cam, int i, int j) {
   RayOut res{0.0, 0.0f, 0};
 
@@ -112,14 +112,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   const void* v0 = cam.vel[0];
   const void* v1 = cam.vel[1];
   const void* v2 = cam.vel[2];
-  const double lamInv0 = cam.lamInv[0], lamInv1 = cam.lamInv[1], lamInv2 = cam.lamInv[2];
-  const double invD0 = cam.invD[0], invD1 = cam.invD[1], invD2 = cam.invD[2];
-  const float lamInvF0 = cam.lamInvF[0], lamInvF1 = cam.lamInvF[1], lamInvF2 = cam.lamInvF[2];
-  const float invDF0 = cam.invDF[0], invDF1 = cam.invDF[1], invDF2 = cam.invDF[2];
   const int s0 = D[0] > 0 ? 1 : -1, s1 = D[1] > 0 ? 1 : -1, s2 = D[2] > 0 ? 1 : -1;
-
-  double eA = sel3(ea, lamInv0, lamInv1, lamInv2);     // lam / |D| of the entry axis
-  float eAF = sel3(ea, lamInvF0, lamInvF1, lamInvF2);
+  const float lf0 = cam.lamInvF[0], lf1 = cam.lamInvF[1], lf2 = cam.lamInvF[2];
+  const float if0 = cam.invDF[0], if1 = cam.invDF[1], if2 = cam.invDF[2];
 
   // ---- top-down descent (Sec. 2.2) -----------------------------------------
   uint32_t stack[kMaxLevel + 2];
@@ -132,9 +127,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   bool bad = false;
 
   // Walk down from oct o (level q) to the leaf holding the ray just after the
-  // current entry event.  Levels q <= lref take the cell from the known
-  // coordinates kk (level lref); deeper levels decide each axis by the exact
-  // side of the parent cell's mid-plane.
+  // entry event (m / dA on axis ea).  Levels q <= lref take the cell from the
+  // known coordinates kk (level lref); deeper levels decide each axis by the
+  // exact side of the parent cell's mid-plane.
   auto descend = [&](int q, int lref, int kk0, int kk1, int kk2) {
     for (;;) {
       if (q <= lref) {
@@ -157,91 +152,176 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       o = r.x + __popc(r.y & ((1u << c) - 1u));
       if (o >= A.n_oct) { bad = true; break; }
       ++q;
-      stack[q] = o;
+      if (!NB) stack[q] = o;
       r = __ldg(&rec[o]);
     }
     lvl = q;
   };
 
+  // Exact pairwise order of the current cell's exit times t_x = n_x / |D_x|:
+  //   e_xy = n_x |D_y| - n_y |D_x|   (sign of t_x - t_y),
+  // with n_x the distance (2^-36 units) from the origin to the cell's exit
+  // plane on axis x (n = 1, |D| = 0 for an axis the ray runs parallel to,
+  // which makes its time compare as infinite).  sD_x = |D_x| * cell size.
+  long long e01, e02, e12, sD0, sD1, sD2;
+  auto recompute = [&]() {
+    const int sh = kFixBits - lvl;
+    const long long n0 = D[0] > 0 ? ((long long)(k0 + 1) << sh) - X[0] : (D[0] < 0 ? X[0] - ((long long)k0 << sh) : 1);
+    const long long n1 = D[1] > 0 ? ((long long)(k1 + 1) << sh) - X[1] : (D[1] < 0 ? X[1] - ((long long)k1 << sh) : 1);
+    const long long n2 = D[2] > 0 ? ((long long)(k2 + 1) << sh) - X[2] : (D[2] < 0 ? X[2] - ((long long)k2 << sh) : 1);
+    e01 = n0 * aD[1] - n1 * aD[0];
+    e02 = n0 * aD[2] - n2 * aD[0];
+    e12 = n1 * aD[2] - n2 * aD[1];
+    sD0 = (long long)aD[0] << sh;
+    sD1 = (long long)aD[1] << sh;
+    sD2 = (long long)aD[2] << sh;
+  };
+
   descend(1, 0, 0, 0, 0);
+  recompute();
 
   // ---- accumulators ---------------------------------------------------------
   double Sd = 0.0, Nd = 0.0, Md = 0.0;
   float Sf = 0.0f, cSf = 0.0f, Nf = 0.0f, cNf = 0.0f, Mf = 0.0f;
   int count = 0;
-  const float wf0 = cam.wF[0], wf1 = cam.wF[1], wf2 = cam.wF[2];
-  const double wd0 = cam.w[0], wd1 = cam.w[1], wd2 = cam.w[2];
 
   while (!bad) {
     const size_t cell = (size_t)o * 8 + c;
     const F rho = load_field<F>(rho_base, cell);
 
-    // Exit event of cell k (level lvl): earliest face crossing ahead of the ray.
-    const int sh = kFixBits - lvl;
-    const long long n0 = D[0] > 0 ? ((long long)(k0 + 1) << sh) - X[0] : (D[0] < 0 ? X[0] - ((long long)k0 << sh) : 1);
-    const long long n1 = D[1] > 0 ? ((long long)(k1 + 1) << sh) - X[1] : (D[1] < 0 ? X[1] - ((long long)k1 << sh) : 1);
-    const long long n2 = D[2] > 0 ? ((long long)(k2 + 1) << sh) - X[2] : (D[2] < 0 ? X[2] - ((long long)k2 << sh) : 1);
-    // An axis with D = 0 has n = 1 and |D| = 0: its time compares as +infinity.
-    const int c01 = cmp64(n0 * aD[1], n1 * aD[0]);
-    const long long nw = c01 <= 0 ? n0 : n1;
-    const int aw = c01 <= 0 ? aD[0] : aD[1];
-    const int mw = c01 < 0 ? 1 : (c01 > 0 ? 2 : 3);
-    const int c2 = cmp64(nw * aD[2], n2 * aw);
-    const int step = c2 < 0 ? mw : (c2 == 0 ? (mw | 4) : 4);   // axes crossed together
-    const int b = c2 > 0 ? 2 : (c01 <= 0 ? 0 : 1);              // exit axis
-    const long long nb = c2 > 0 ? n2 : nw;
-    const int db = c2 > 0 ? aD[2] : aw;
-
-    // Chord: exact (t_exit - t_entry) |D_b| |D_a|, times lam / (|D_a| |D_b|).
-    const long long num = nb * dA - m * db;
+    // Exit face(s): the axes whose exit time is the minimum.
+    const bool lt01 = e01 < 0, gt01 = e01 > 0;
+    const bool lt02 = e02 < 0, gt02 = e02 > 0;
+    const bool lt12 = e12 < 0, gt12 = e12 > 0;
+    const bool st0 = !gt01 && !gt02;
+    const bool st1 = !lt01 && !gt12;
+    const bool st2 = !lt02 && !lt12;
+    const int b = st0 ? 0 : (st1 ? 1 : 2);
 
     if (MODE == AMR_MODE_MAX) {
       if (PREC == AMR_PREC_FP64) Md = fmax(Md, (double)rho);
       else Mf = fmaxf(Mf, (float)rho);
-    } else if (PREC == AMR_PREC_FP64) {
-      const double len = (double)num * (eA * sel3(b, invD0, invD1, invD2));
-      const double wgt = (double)rho * len;
-      Sd += wgt;
-      if (MODE == AMR_MODE_WMEAN) {
-        const double vlos = (double)load_field<F>(v0, cell) * wd0 + (double)load_field<F>(v1, cell) * wd1 +
-                            (double)load_field<F>(v2, cell) * wd2;
-        Nd += wgt * vlos;
-      }
     } else {
-      const float len = __fmul_rn(__ll2float_rn(num), __fmul_rn(eAF, sel3(b, invDF0, invDF1, invDF2)));
-      const float wgt = __fmul_rn((float)rho, len);
-      if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
-      else Sf = __fadd_rn(Sf, wgt);
-      if (MODE == AMR_MODE_WMEAN) {
-        const float vlos = (float)load_field<F>(v0, cell) * wf0 + (float)load_field<F>(v1, cell) * wf1 +
-                           (float)load_field<F>(v2, cell) * wf2;
-        const float nv = __fmul_rn(wgt, vlos);
-        if (PREC == AMR_PREC_FP32_KAHAN) neumaier_add(Nf, cNf, nv);
-        else Nf = __fadd_rn(Nf, nv);
+      // Chord.  The cell was entered on its face on axis ea, at n_ea - size, so
+      //   (t_exit - t_entry) |D_ea| |D_b| = sD_b - (n_ea |D_b| - n_b |D_ea|)   (b != ea)
+      //   (t_exit - t_entry) = size / |D_b|                                     (b == ea)
+      const int pair = ea + b - 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
+      const long long ep = sel3(pair, e01, e02, e12);
+      const long long num = sel3(b, sD0, sD1, sD2) - (ea < b ? ep : -ep);
+      const int e2 = kFixBits - lvl;  // size = 2^e2
+      if (PREC == AMR_PREC_FP64) {
+        const double lb = cam.lamInv[b];
+        const double len = (b == ea) ? lb * __longlong_as_double((long long)(1023 + e2) << 52)
+                                     : (double)num * (cam.lamInv[ea] * cam.invD[b]);
+        const double wgt = (double)rho * len;
+        Sd += wgt;
+        if (MODE == AMR_MODE_WMEAN) {
+          const double vlos = (double)load_field<F>(v0, cell) * cam.w[0] + (double)load_field<F>(v1, cell) * cam.w[1] +
+                              (double)load_field<F>(v2, cell) * cam.w[2];
+          Nd += wgt * vlos;
+        }
+      } else {
+        const float lb = sel3(b, lf0, lf1, lf2);
+        const float len = (b == ea) ? __fmul_rn(lb, __int_as_float((127 + e2) << 23))
+                                    : __fmul_rn(__ll2float_rn(num), __fmul_rn(sel3(ea, lf0, lf1, lf2), sel3(b, if0, if1, if2)));
+        const float wgt = __fmul_rn((float)rho, len);
+        if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
+        else Sf = __fadd_rn(Sf, wgt);
+        if (MODE == AMR_MODE_WMEAN) {
+          const float vlos = (float)load_field<F>(v0, cell) * cam.wF[0] + (float)load_field<F>(v1, cell) * cam.wF[1] +
+                             (float)load_field<F>(v2, cell) * cam.wF[2];
+          const float nv = __fmul_rn(wgt, vlos);
+          if (PREC == AMR_PREC_FP32_KAHAN) neumaier_add(Nf, cNf, nv);
+          else Nf = __fadd_rn(Nf, nv);
+        }
       }
     }
     ++count;
-
-    // The exit becomes the next entry event.
-    m = nb;
-    dA = db;
-    eA = sel3(b, lamInv0, lamInv1, lamInv2);
-    eAF = sel3(b, lamInvF0, lamInvF1, lamInvF2);
+    ea = b;
 
     // Neighbour at this level; leaving [0, 2^lvl) on any axis ends the ray.
-    const int j0 = k0 + ((step & 1) ? s0 : 0);
-    const int j1 = k1 + ((step & 2) ? s1 : 0);
-    const int j2 = k2 + ((step & 4) ? s2 : 0);
+    const int j0 = k0 + (st0 ? s0 : 0);
+    const int j1 = k1 + (st1 ? s1 : 0);
+    const int j2 = k2 + (st2 ? s2 : 0);
     const unsigned lim = 1u << lvl;
     if ((unsigned)j0 >= lim || (unsigned)j1 >= lim || (unsigned)j2 >= lim) break;
-    // Deepest oct holding both cells: highest differing coordinate bit.
-    const int h = 31 - __clz((k0 ^ j0) | (k1 ^ j1) | (k2 ^ j2));
-    const int q = lvl - h;
-    if (h > 0) {
-      o = stack[q];
+    // Exit planes of the stepped axes move one cell on (valid while the level holds).
+    e01 += (st0 ? sD1 : 0) - (st1 ? sD0 : 0);
+    e02 += (st0 ? sD2 : 0) - (st2 ? sD0 : 0);
+    e12 += (st1 ? sD2 : 0) - (st2 ? sD1 : 0);
+    const int diff = (k0 ^ j0) | (k1 ^ j1) | (k2 ^ j2);
+    const int lvl0 = lvl;
+    if (diff == 1) {
+      // Same oct: flip the stepped bits of the cell index.
+      k0 = j0; k1 = j1; k2 = j2;
+      c ^= (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
+      if (!((r.y >> c) & 1u) || lvl >= L) {
+        if (count >= kStepCap) { atomicExch(&A.q->error, (int)kDevStepCap); break; }
+        continue;
+      }
+      // The neighbour is refined: enter its child oct and go on down by mid-planes.
+      const int sh = kFixBits - lvl;
+      const int ka = sel3(ea, k0, k1, k2);
+      const long long Xa = sel3(ea, X[0], X[1], X[2]);
+      m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+      dA = sel3(ea, aD[0], aD[1], aD[2]);
+      o = r.x + __popc(r.y & ((1u << c) - 1u));
+      if (o >= A.n_oct) { bad = true; break; }
+      if (!NB) stack[lvl + 1] = o;
       r = __ldg(&rec[o]);
+      descend(lvl + 1, lvl, j0, j1, j2);
+    } else if (NB && !(st0 + st1 + st2 > 1)) {
+      // One axis leaves the oct: follow its face link (same-level oct, or the
+      // coarser leaf covering that side).
+      const int f = 2 * b + (sel3(b, s0, s1, s2) > 0 ? 1 : 0);
+      const int v = __ldg(&A.nbr[(size_t)o * 6 + f]);
+      k0 = j0; k1 = j1; k2 = j2;
+      if (v >= 0) {
+        o = (uint32_t)v;
+        if (o >= A.n_oct) { bad = true; break; }
+        r = __ldg(&rec[o]);
+        c ^= 1 << b;
+        if (((r.y >> c) & 1u) && lvl < L) {
+          const int sh = kFixBits - lvl;
+          const int ka = sel3(ea, k0, k1, k2);
+          const long long Xa = sel3(ea, X[0], X[1], X[2]);
+          m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+          dA = sel3(ea, aD[0], aD[1], aD[2]);
+          o = r.x + __popc(r.y & ((1u << c) - 1u));
+          if (o >= A.n_oct) { bad = true; break; }
+          r = __ldg(&rec[o]);
+          descend(lvl + 1, lvl, j0, j1, j2);
+        }
+      } else {
+        if (v == -1) { bad = true; break; }
+        const int cr = -v - 2;
+        o = (uint32_t)cr >> 3;
+        if (o >= A.n_oct) { bad = true; break; }
+        c = cr & 7;
+        r = __ldg(&rec[o]);
+        lvl = (int)((r.y >> 8) & 31u);
+        if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
+        k0 >>= lvl0 - lvl; k1 >>= lvl0 - lvl; k2 >>= lvl0 - lvl;
+      }
+    } else {
+      // Several axes at once (an edge or corner): from the deepest shared
+      // ancestor on the stack, or from the root when there is no stack.
+      int q = 1;
+      if (NB) {
+        o = 0;
+      } else {
+        q = lvl - (31 - __clz(diff));
+        o = stack[q];
+      }
+      r = __ldg(&rec[o]);
+      const int sh = kFixBits - lvl;
+      const int ka = sel3(ea, j0, j1, j2);
+      const long long Xa = sel3(ea, X[0], X[1], X[2]);
+      m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+      dA = sel3(ea, aD[0], aD[1], aD[2]);
+      descend(q, lvl, j0, j1, j2);
     }
-    descend(q, lvl, j0, j1, j2);
+    if (lvl != lvl0) recompute();
     if (count >= kStepCap) {
       atomicExch(&A.q->error, (int)kDevStepCap);
       break;
@@ -271,13 +351,13 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   return res;
 }
 
-template <int PREC, typename F>
+template <int PREC, bool NB, typename F>
 __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& cam, int i, int j) {
   RayOut o;
   switch (cam.mode) {
-    case AMR_MODE_COLUMN: o = trace_ray<PREC, AMR_MODE_COLUMN, F>(A, cam, i, j); break;
-    case AMR_MODE_WMEAN: o = trace_ray<PREC, AMR_MODE_WMEAN, F>(A, cam, i, j); break;
-    default: o = trace_ray<PREC, AMR_MODE_MAX, F>(A, cam, i, j); break;
+    case AMR_MODE_COLUMN: o = trace_ray<PREC, AMR_MODE_COLUMN, NB, F>(A, cam, i, j); break;
+    case AMR_MODE_WMEAN: o = trace_ray<PREC, AMR_MODE_WMEAN, NB, F>(A, cam, i, j); break;
+    default: o = trace_ray<PREC, AMR_MODE_MAX, NB, F>(A, cam, i, j); break;
   }
   const size_t px = (size_t)j * cam.nx + i;
   if (PREC == AMR_PREC_FP64) static_cast<double*>(cam.map)[px] = o.d;
@@ -289,8 +369,8 @@ __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& ca
 // Persistent batch kernel: each warp repeatedly takes `tiles_per_grab` ray tiles
 // from the queue head; a tile index is mapped to its camera by binary search
 // over the per-camera tile prefix sums.
-template <int PREC, typename F>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
+template <int PREC, bool NB, typename F>
+__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long segs = 0;
   for (;;) {
@@ -312,7 +392,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
       const int tx = lt % tiles_x, ty = lt / tiles_x;
       const int i = tx * A.tile_w + lane % A.tile_w;
       const int j = ty * A.tile_h + lane / A.tile_w;
-      if (i < cam.nx && j < cam.ny) segs += (unsigned)render_pixel<PREC, F>(A, cam, i, j);
+      if (i < cam.nx && j < cam.ny) segs += (unsigned)render_pixel<PREC, NB, F>(A, cam, i, j);
     }
   }
 #pragma unroll
@@ -320,40 +400,40 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs A) {
   if (lane == 0 && segs) atomicAdd(&A.q->segments, segs);
 }
 
-template <int PREC, typename F>
+template <int PREC, bool NB, typename F>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&batch_kernel<PREC, F>);
+  return reinterpret_cast<const void*>(&batch_kernel<PREC, NB, F>);
 }
 
-const void* pick(int prec, bool f64) {
-  if (f64) {
-    switch (prec) {
-      case AMR_PREC_FP64: return kernel_ptr<AMR_PREC_FP64, double>();
-      case AMR_PREC_FP32_KAHAN: return kernel_ptr<AMR_PREC_FP32_KAHAN, double>();
-      default: return kernel_ptr<AMR_PREC_FP32_PLAIN, double>();
-    }
-  }
+template <bool NB, typename F>
+const void* pick_prec(int prec) {
   switch (prec) {
-    case AMR_PREC_FP64: return kernel_ptr<AMR_PREC_FP64, float>();
-    case AMR_PREC_FP32_KAHAN: return kernel_ptr<AMR_PREC_FP32_KAHAN, float>();
-    default: return kernel_ptr<AMR_PREC_FP32_PLAIN, float>();
+    case AMR_PREC_FP64: return kernel_ptr<AMR_PREC_FP64, NB, F>();
+    case AMR_PREC_FP32_KAHAN: return kernel_ptr<AMR_PREC_FP32_KAHAN, NB, F>();
+    default: return kernel_ptr<AMR_PREC_FP32_PLAIN, NB, F>();
   }
+}
+
+// nb: the launch carries face-neighbour links.
+const void* pick(int prec, bool f64, bool nb) {
+  if (nb) return f64 ? pick_prec<true, double>(prec) : pick_prec<true, float>(prec);
+  return f64 ? pick_prec<false, double>(prec) : pick_prec<false, float>(prec);
 }
 
 }  // namespace
 
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s) {
   void* args[] = {const_cast<BatchArgs*>(&a)};
-  return cudaLaunchKernel(pick(prec, f64), dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchKernel(pick(prec, f64, a.nbr != nullptr), dim3(grid), dim3(block), args, 0, s);
 }
 
-cudaError_t batch_occupancy(int prec, bool f64, int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, f64), block, 0);
+cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, f64, nb), block, 0);
 }
 
-int batch_regs(int prec, bool f64) {
+int batch_regs(int prec, bool f64, bool nb) {
   cudaFuncAttributes at{};
-  if (cudaFuncGetAttributes(&at, pick(prec, f64)) != cudaSuccess) return -1;
+  if (cudaFuncGetAttributes(&at, pick(prec, f64, nb)) != cudaSuccess) return -1;
   return at.numRegs;
 }
 

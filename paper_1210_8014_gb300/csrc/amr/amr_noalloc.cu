@@ -160,7 +160,7 @@ extern "C" amr_status amr_render_batch_noalloc(int64_t n_oct, const uint64_t* re
     a.tiles_per_grab = 1;
     a.q = d_q + g;
     int bps = 1;
-    e = amr::batch_occupancy(g, f64, block, &bps);
+    e = amr::batch_occupancy(g, f64, false, block, &bps);
     if (e != cudaSuccess) break;
     const int64_t blocks_needed = (total[g] * 32 + block - 1) / block;
     int64_t grid = (int64_t)sms * (bps > 0 ? bps : 1);
