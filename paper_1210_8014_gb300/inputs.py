@@ -340,8 +340,9 @@ def batch_cameras(tree: Tree, n_cams=64, precision=PREC_FP32_KAHAN, seed=3):
 
 
 # Relative mass threshold of the level-22 zoom tree, picked once by bisection on
-# the generator's leaf count (target ~200M leaves); see zoom_tree().
-ZOOM_THRESHOLD = 2.0 ** -25
+# the generator's leaf count (target ~200M leaves): 2^-24 gives 57.7M leaves,
+# 2^-25 116.8M, 2^-25.75 193.2M (27.6M octs, leaves at levels 7-22).
+ZOOM_THRESHOLD = 2.0 ** -25.75
 
 
 def zoom_tree(dtype=np.float32, threshold=ZOOM_THRESHOLD) -> Tree:
@@ -355,6 +356,14 @@ def zoom_cameras(tree: Tree, n_frames=8, n=4096, precision=PREC_FP32_KAHAN):
     w = random_direction(rng)
     return [camera_along(w, centre=(0.5, 0.5, 0.5), fov=2.0 ** -f, n=n, max_level=LEVEL_AUTO,
                          mode=MODE_COLUMN, precision=precision) for f in range(n_frames)]
+
+
+def deep_centre_camera(tree: Tree, n=512, precision=PREC_FP32_KAHAN, mode=MODE_COLUMN):
+    """Full-depth view of the galactic centre: fov 2^-13 at 512^2 puts the pixel
+    rule at level 22."""
+    rng = np.random.default_rng(44)
+    return camera_along(random_direction(rng), centre=(0.5, 0.5, 0.5), fov=2.0 ** -13, n=n, max_level=LEVEL_AUTO,
+                        mode=mode, precision=precision)
 
 
 def request_stream(tree: Tree, duration_s=60.0, rate=50.0, seed=5, precision=PREC_FP32_KAHAN):

@@ -1,0 +1,66 @@
+"""Full-size workloads in the launch configuration bench.py times, checked on
+sampled pixels against the oracle (pytest -m gpu).
+
+- the 64-camera batch on the 16M-leaf galaxy octree (one persistent launch per
+  precision, as bench.py launches it): FP32 compensated and FP64;
+- the 8-frame 4096^2 zoom on the 193M-leaf level-22 octree, FP32 compensated;
+- a full-depth level-22 view of the centre (512^2, fov 2^-13).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from parity import assert_parity
+from paper_1210_8014_gb300 import amr, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def sample(cam, k, rng):
+    return rng.integers(0, cam.nx, k), rng.integers(0, cam.ny, k)
+
+
+def check_batch(r, tree, cams, per_cam, seed):
+    outs = r.render_batch(cams)
+    torch.cuda.synchronize()
+    prepared = oracle.prepare(tree)
+    rng = np.random.default_rng(seed)
+    for q, (cam, (m, c)) in enumerate(zip(cams, outs)):
+        pi, pj = sample(cam, per_cam, rng)
+        ref, rc = oracle.render(prepared, cam, pixels=(pi, pj))
+        mh = m.cpu().numpy()[pj, pi]
+        ch = c.cpu().numpy()[pj, pi]
+        assert_parity(cam.mode, cam.precision, mh, ch, ref, rc, ctx=f"camera {q} ({cam.nx}^2 mode {cam.mode})")
+    return outs
+
+
+def test_batch_64_cameras_full_size(gpu):
+    tree = inputs.batch_tree()
+    cams = inputs.batch_cameras(tree)
+    with amr.Renderer(tree) as r:
+        check_batch(r, tree, cams, 48, seed=1)
+        check_batch(r, tree, [c.with_(precision=amr.AMR_PREC_FP64) for c in cams], 24, seed=2)
+        st = r.stats()
+        assert st["device_errors"] == 0
+
+
+def test_zoom_level22_full_size(gpu):
+    tree = inputs.zoom_tree()
+    assert tree.depth == 22 and 190e6 <= tree.n_leaves <= 210e6
+    cams = inputs.zoom_cameras(tree)
+    with amr.Renderer(tree) as r:
+        levels = [amr.amr_camera_check(r.ctx, c) for c in cams]
+        assert levels == list(range(12, 20))
+        check_batch(r, tree, cams, 96, seed=3)
+        deep = [inputs.deep_centre_camera(tree, mode=m) for m in (0, 2)]
+        assert amr.amr_camera_check(r.ctx, deep[0]) == 22
+        check_batch(r, tree, deep, 2000, seed=4)
+        assert r.stats()["device_errors"] == 0
