@@ -68,6 +68,8 @@ struct LaunchSlot {
   cudaEvent_t start = nullptr, done = nullptr;
   bool pending = false;  // a launch whose results are not yet harvested
   int n_groups = 0;
+  cudaGraphExec_t gexec = nullptr;  // captured launch sequence of this slot
+  std::vector<int64_t> gkey;        // batch shape it was captured for
 };
 
 struct Request {
@@ -107,6 +109,8 @@ struct amr_ctx {
   int64_t n_dev_errors = 0;
   double last_batch_ms = 0.0;
   double autotune_ms = -1.0;
+  int64_t n_graph_captures = 0, n_graph_launches = 0;
+  int occupancy[amr::kMaxPrecisions][2][33] = {};  // resident blocks per SM, by precision, dtype, block/32
   // server
   std::mutex srv_mu;
   std::condition_variable srv_cv;   // work arrived / budget freed / stop
@@ -132,6 +136,7 @@ namespace {
 constexpr int kSlots = 8;
 
 void free_slot(LaunchSlot& s) {
+  if (s.gexec) cudaGraphExecDestroy(s.gexec);
   if (s.h_cams) cudaFreeHost(s.h_cams);
   if (s.h_tiles) cudaFreeHost(s.h_tiles);
   if (s.h_q) cudaFreeHost(s.h_q);
@@ -143,6 +148,9 @@ void free_slot(LaunchSlot& s) {
 
 amr_status grow_slot(LaunchSlot& s, int n) {
   if (s.cap >= n && s.h_cams) return AMR_OK;
+  if (s.gexec) cudaGraphExecDestroy(s.gexec);
+  s.gexec = nullptr;
+  s.gkey.clear();
   int cap = std::max(n, std::max(64, s.cap * 2));
   if (s.h_cams) cudaFreeHost(s.h_cams);
   if (s.h_tiles) cudaFreeHost(s.h_tiles);
@@ -353,15 +361,13 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     if (acc >= (int64_t(1) << 31) - 4096) return fail(AMR_E_INVALID, "batch too large: %lld tiles", (long long)acc);
     tiles_total[g] = acc;
   }
-  CUDA_TRY(cudaEventRecord(s.start, stream));
-  CUDA_TRY(cudaMemcpyAsync(s.d_cams, s.h_cams, n * sizeof(CamDev), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemcpyAsync(s.d_tiles, s.h_tiles, (size_t)amr::kMaxPrecisions * (s.cap + 1) * sizeof(int32_t),
-                           cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), stream));
-  s.n_groups = amr::kMaxPrecisions;
+  // Launch plan: one persistent launch per precision group present.
+  amr::BatchArgs args[amr::kMaxPrecisions];
+  int grids[amr::kMaxPrecisions] = {0, 0, 0};
   for (int g = 0; g < amr::kMaxPrecisions; ++g) {
     if (!groups[g] || !tiles_total[g]) continue;
-    amr::BatchArgs a{};
+    amr::BatchArgs& a = args[g];
+    a = amr::BatchArgs{};
     a.rec = ctx->tree.rec;
     a.nbr = ctx->tree.nbr;
     a.n_oct = (uint32_t)ctx->tree.n_oct;
@@ -375,17 +381,68 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     a.q = s.d_q + g;
     int bps = opt.blocks_per_sm;
     if (bps <= 0) {
-      CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, true, opt.block_threads, &bps));
-      bps = std::max(1, bps);
+      int& cached = ctx->occupancy[g][ctx->tree.f64 ? 1 : 0][opt.block_threads / 32];
+      if (cached <= 0) CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, true, opt.block_threads, &cached));
+      bps = std::max(1, cached);
     }
     int64_t grid = (int64_t)ctx->sms * bps;
     const int64_t warps_needed = (tiles_total[g] + opt.tiles_per_grab - 1) / opt.tiles_per_grab;
     const int64_t blocks_needed = (warps_needed * 32 + opt.block_threads - 1) / opt.block_threads;
-    grid = std::max<int64_t>(1, std::min(grid, blocks_needed));
-    CUDA_TRY(amr::launch_batch(g, ctx->tree.f64, a, (int)grid, opt.block_threads, stream));
+    grids[g] = (int)std::max<int64_t>(1, std::min(grid, blocks_needed));
   }
-  CUDA_TRY(cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, stream));
-  CUDA_TRY(cudaEventRecord(s.done, stream));
+  const size_t tile_bytes = (size_t)amr::kMaxPrecisions * (s.cap + 1) * sizeof(int32_t);
+  // In a capture the two events must become event-record nodes of the graph
+  // (external records), not capture-internal dependencies.
+  auto record = [&](cudaStream_t st, bool capturing) -> cudaError_t {
+    const unsigned ev = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaError_t e = cudaEventRecordWithFlags(s.start, st, ev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_cams, s.h_cams, n * sizeof(CamDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_tiles, s.h_tiles, tile_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), st);
+    for (int g = 0; g < amr::kMaxPrecisions && e == cudaSuccess; ++g)
+      if (grids[g]) e = amr::launch_batch(g, ctx->tree.f64, args[g], grids[g], opt.block_threads, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(s.done, st, ev);
+    return e;
+  };
+  s.n_groups = amr::kMaxPrecisions;
+  if (opt.use_graph) {
+    // Replay a captured graph of this slot when the batch shape is unchanged
+    // (the camera table itself is read from the slot's pinned staging).
+    std::vector<int64_t> key = {n, s.cap, (int64_t)(uintptr_t)s.d_cams, (int64_t)(uintptr_t)ctx->tree.rec,
+                                (int64_t)(uintptr_t)ctx->tree.nbr, ctx->tree.f64, opt.block_threads,
+                                opt.tile_w, opt.tile_h, opt.tiles_per_grab};
+    for (int g = 0; g < amr::kMaxPrecisions; ++g) {
+      key.push_back(groups[g]);
+      key.push_back(tiles_total[g]);
+      key.push_back(grids[g]);
+    }
+    if (!s.gexec || s.gkey != key) {
+      if (s.gexec) cudaGraphExecDestroy(s.gexec);
+      s.gexec = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = record(ctx->stream, true);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(AMR_E_CUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&s.gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        s.gexec = nullptr;
+        return fail(AMR_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      }
+      s.gkey = key;
+      ctx->n_graph_captures++;
+    }
+    CUDA_TRY(cudaGraphLaunch(s.gexec, stream));
+    ctx->n_graph_launches++;
+  } else {
+    CUDA_TRY(record(stream, false));
+  }
   s.pending = true;
   ctx->n_renders++;
   ctx->n_cams += n;
@@ -1058,14 +1115,14 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       "{\"renders\": %lld, \"cameras\": %lld, \"rays\": %lld, \"segments\": %llu, \"device_errors\": %lld, "
       "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d}, "
       "\"options\": {\"tile_w\": %d, \"tile_h\": %d, \"block_threads\": %d, \"blocks_per_sm\": %d, "
-      "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, "
+      "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
       "\"regs\": {\"fp64\": %d, \"fp32_kahan\": %d, \"fp32_plain\": %d}, \"sms\": %d, "
       "\"server\": {\"done\": %lld, \"failed\": %lld, \"batches\": %lld, \"max_inflight\": %lld, \"queued\": %lld, "
       "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
       (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
       (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
-      o.use_graph, ctx->autotune_ms, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
+      o.use_graph, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
       fps);
   if (len < 0) return fail(AMR_E_INVALID, "stats formatting failed");
