@@ -113,6 +113,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   const void* v1 = cam.vel[1];
   const void* v2 = cam.vel[2];
   const int s0 = D[0] > 0 ? 1 : -1, s1 = D[1] > 0 ? 1 : -1, s2 = D[2] > 0 ? 1 : -1;
+  // Bit a set: the ray moves down axis a (its cells are entered from the high side).
+  const int dirbits = (s0 < 0 ? 1 : 0) | (s1 < 0 ? 2 : 0) | (s2 < 0 ? 4 : 0);
   const float lf0 = cam.lamInvF[0], lf1 = cam.lamInvF[1], lf2 = cam.lamInvF[2];
   const float if0 = cam.invDF[0], if1 = cam.invDF[1], if2 = cam.invDF[2];
 
@@ -239,49 +241,45 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     ++count;
     ea = b;
 
-    // Neighbour at this level; leaving [0, 2^lvl) on any axis ends the ray.
-    const int j0 = k0 + (st0 ? s0 : 0);
-    const int j1 = k1 + (st1 ? s1 : 0);
-    const int j2 = k2 + (st2 ? s2 : 0);
-    const unsigned lim = 1u << lvl;
-    if ((unsigned)j0 >= lim || (unsigned)j1 >= lim || (unsigned)j2 >= lim) break;
     // Exit planes of the stepped axes move one cell on (valid while the level holds).
-    e01 += (st0 ? sD1 : 0) - (st1 ? sD0 : 0);
-    e02 += (st0 ? sD2 : 0) - (st2 ? sD0 : 0);
-    e12 += (st1 ? sD2 : 0) - (st2 ? sD1 : 0);
-    const int diff = (k0 ^ j0) | (k1 ^ j1) | (k2 ^ j2);
+    if (st0) { e01 += sD1; e02 += sD2; }
+    if (st1) { e01 -= sD0; e12 += sD2; }
+    if (st2) { e02 -= sD0; e12 -= sD1; }
+    const int stepbits = (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
     const int lvl0 = lvl;
-    if (diff == 1) {
-      // Same oct: flip the stepped bits of the cell index.
-      k0 = j0; k1 = j1; k2 = j2;
-      c ^= (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
-      if (!((r.y >> c) & 1u) || lvl >= L) {
-        if (count >= kStepCap) { atomicExch(&A.q->error, (int)kDevStepCap); break; }
-        continue;
-      }
-      // The neighbour is refined: enter its child oct and go on down by mid-planes.
-      const int sh = kFixBits - lvl;
-      const int ka = sel3(ea, k0, k1, k2);
-      const long long Xa = sel3(ea, X[0], X[1], X[2]);
-      m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
-      dA = sel3(ea, aD[0], aD[1], aD[2]);
-      o = r.x + __popc(r.y & ((1u << c) - 1u));
-      if (o >= A.n_oct) { bad = true; break; }
-      if (!NB) stack[lvl + 1] = o;
-      r = __ldg(&rec[o]);
-      descend(lvl + 1, lvl, j0, j1, j2);
-    } else if (NB && !(st0 + st1 + st2 > 1)) {
-      // One axis leaves the oct: follow its face link (same-level oct, or the
-      // coarser leaf covering that side).
-      const int f = 2 * b + (sel3(b, s0, s1, s2) > 0 ? 1 : 0);
-      const int v = __ldg(&A.nbr[(size_t)o * 6 + f]);
-      k0 = j0; k1 = j1; k2 = j2;
-      if (v >= 0) {
-        o = (uint32_t)v;
-        if (o >= A.n_oct) { bad = true; break; }
-        r = __ldg(&rec[o]);
-        c ^= 1 << b;
-        if (((r.y >> c) & 1u) && lvl < L) {
+    if (NB) {
+      // Neighbour at this level.  A step stays inside the oct when every
+      // stepped axis moves from the oct's low cell up or from its high cell down.
+      const bool inoct = ((c ^ dirbits) & stepbits) == 0;
+      if (inoct || !(stepbits & (stepbits - 1))) {
+        if (st0) k0 += s0;
+        if (st1) k1 += s1;
+        if (st2) k2 += s2;
+        c ^= stepbits;
+        bool coarser = false;
+        if (!inoct) {
+          // One axis leaves the oct: its face link is the same-level oct there,
+          // the coarser leaf covering that side, or -1 where the box ends.
+          const int v = __ldg(&A.nbr[(size_t)o * 6 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
+          if (v == -1) break;
+          if (v >= 0) {
+            o = (uint32_t)v;
+            if (o >= A.n_oct) { bad = true; break; }
+            r = __ldg(&rec[o]);
+          } else {
+            const int cr = -v - 2;
+            o = (uint32_t)cr >> 3;
+            if (o >= A.n_oct) { bad = true; break; }
+            c = cr & 7;
+            r = __ldg(&rec[o]);
+            lvl = (int)((r.y >> 8) & 31u);
+            if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
+            k0 >>= lvl0 - lvl; k1 >>= lvl0 - lvl; k2 >>= lvl0 - lvl;
+            coarser = true;
+          }
+        }
+        if (!coarser && ((r.y >> c) & 1u) && lvl < L) {
+          // The neighbour is refined: enter its child oct, go on down by mid-planes.
           const int sh = kFixBits - lvl;
           const int ka = sel3(ea, k0, k1, k2);
           const long long Xa = sel3(ea, X[0], X[1], X[2]);
@@ -290,36 +288,59 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           o = r.x + __popc(r.y & ((1u << c) - 1u));
           if (o >= A.n_oct) { bad = true; break; }
           r = __ldg(&rec[o]);
+          descend(lvl + 1, lvl, k0, k1, k2);
+        }
+      } else {
+        // Several axes at once, leaving the oct (an edge or corner): from the root.
+        const int j0 = k0 + (st0 ? s0 : 0);
+        const int j1 = k1 + (st1 ? s1 : 0);
+        const int j2 = k2 + (st2 ? s2 : 0);
+        const unsigned lim = 1u << lvl;
+        if ((unsigned)j0 >= lim || (unsigned)j1 >= lim || (unsigned)j2 >= lim) break;
+        o = 0;
+        r = __ldg(&rec[0]);
+        const int sh = kFixBits - lvl;
+        const int ka = sel3(ea, j0, j1, j2);
+        const long long Xa = sel3(ea, X[0], X[1], X[2]);
+        m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+        dA = sel3(ea, aD[0], aD[1], aD[2]);
+        descend(1, lvl, j0, j1, j2);
+      }
+    } else {
+      // No links: neighbour by coordinates; leaving [0, 2^lvl) ends the ray.
+      const int j0 = k0 + (st0 ? s0 : 0);
+      const int j1 = k1 + (st1 ? s1 : 0);
+      const int j2 = k2 + (st2 ? s2 : 0);
+      const unsigned lim = 1u << lvl;
+      if ((unsigned)j0 >= lim || (unsigned)j1 >= lim || (unsigned)j2 >= lim) break;
+      const int diff = (k0 ^ j0) | (k1 ^ j1) | (k2 ^ j2);
+      k0 = j0; k1 = j1; k2 = j2;
+      if (diff == 1) {
+        c ^= stepbits;
+        if (((r.y >> c) & 1u) && lvl < L) {
+          const int sh = kFixBits - lvl;
+          const int ka = sel3(ea, k0, k1, k2);
+          const long long Xa = sel3(ea, X[0], X[1], X[2]);
+          m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+          dA = sel3(ea, aD[0], aD[1], aD[2]);
+          o = r.x + __popc(r.y & ((1u << c) - 1u));
+          if (o >= A.n_oct) { bad = true; break; }
+          stack[lvl + 1] = o;
+          r = __ldg(&rec[o]);
           descend(lvl + 1, lvl, j0, j1, j2);
         }
       } else {
-        if (v == -1) { bad = true; break; }
-        const int cr = -v - 2;
-        o = (uint32_t)cr >> 3;
-        if (o >= A.n_oct) { bad = true; break; }
-        c = cr & 7;
-        r = __ldg(&rec[o]);
-        lvl = (int)((r.y >> 8) & 31u);
-        if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
-        k0 >>= lvl0 - lvl; k1 >>= lvl0 - lvl; k2 >>= lvl0 - lvl;
-      }
-    } else {
-      // Several axes at once (an edge or corner): from the deepest shared
-      // ancestor on the stack, or from the root when there is no stack.
-      int q = 1;
-      if (NB) {
-        o = 0;
-      } else {
-        q = lvl - (31 - __clz(diff));
+        // From the deepest ancestor both cells share (highest differing bit).
+        const int q = lvl - (31 - __clz(diff));
         o = stack[q];
+        r = __ldg(&rec[o]);
+        const int sh = kFixBits - lvl;
+        const int ka = sel3(ea, j0, j1, j2);
+        const long long Xa = sel3(ea, X[0], X[1], X[2]);
+        m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+        dA = sel3(ea, aD[0], aD[1], aD[2]);
+        descend(q, lvl, j0, j1, j2);
       }
-      r = __ldg(&rec[o]);
-      const int sh = kFixBits - lvl;
-      const int ka = sel3(ea, j0, j1, j2);
-      const long long Xa = sel3(ea, X[0], X[1], X[2]);
-      m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
-      dA = sel3(ea, aD[0], aD[1], aD[2]);
-      descend(q, lvl, j0, j1, j2);
     }
     if (lvl != lvl0) recompute();
     if (count >= kStepCap) {
