@@ -36,6 +36,16 @@ sys.path.insert(0, str(ROOT))
 METRIC = "Gsegments/s (FP32-Kahan batch; FP64 kernel and rel err vs FP64 reported beside)"
 UNIT = "Gsegments/s"
 BYTES_PER_SEG = {0: 8, 1: 20, 2: 8}   # child word + scalars per segment, float32 fields
+# Essential lane operations per segment of the exact incremental step (FP32
+# compensated kernel), by mode: exit face 6, chord 5, accumulate 5, error-term
+# update 4, neighbour 4, leaf test 3, field fetch 2, count 1 = 30 (column);
+# max replaces chord + accumulate by one fmax (21); wmean adds three loads, the
+# dot product, a multiply and the Neumaier sum (43).
+OPS_PER_SEG = {0: 30, 1: 43, 2: 21}
+# 152 SMs x 128 lanes x 2.07 GHz: one lane operation per lane per clock.
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+FP64_OPS_PER_SEG = 6       # int64->f64, two multiplies for the chord, float->double, multiply, add
+FP64_PEAK_TFLOPS = 1.25    # nominal GB300 FP64 rate
 
 
 def parse():
@@ -349,6 +359,9 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (ms32 * 1e-3) / 1e9
+    algo_ops = sum(s_ * OPS_PER_SEG[c.mode] for s_, c in zip(seg_cam, cams32))
+    alu_achieved = algo_ops / (ms32 * 1e-3) / 1e12
+    fp64_achieved = segs * FP64_OPS_PER_SEG / (ms64 * 1e-3) / 1e12
     stats = r.stats()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -358,12 +371,19 @@ def run_ours(args):
                    "segments_per_step": segs, "l2": "256 MiB buffer written between timed steps",
                    "options": tuned or amr.amr_get_options(r.ctx).as_dict(), "parallelism": f"replicas{world}"},
         "ms_per_frame": ms32 / len(cams32),
-        "fp64_kernel": {"value": value64, "ms_per_step": ms64, "unit": UNIT},
+        "fp64_kernel": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
+                        "roofline": {"bound": "fp64", "achieved": fp64_achieved, "peak": FP64_PEAK_TFLOPS,
+                                     "unit": "TFLOP/s", "frac": fp64_achieved / FP64_PEAK_TFLOPS,
+                                     "peak_kind": "nominal", "ops_per_segment": FP64_OPS_PER_SEG}},
         "fp32_over_fp64": value / world / value64,
         "fp32_vs_fp64_err": err,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(args.config), "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": algo_bytes},
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                     "frac": alu_achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(args.config),
+                     "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz", "ops_per_segment": OPS_PER_SEG,
+                     "algorithmic_ops_per_launch": algo_ops,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                             "bytes_per_segment": BYTES_PER_SEG}},
         "e2e": {"value": segs / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,
