@@ -178,6 +178,21 @@ def recorded_traffic(config):
         return None
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest value of x over all ranks (the step time every rank waits for)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(segments_per_rank: int, ms_max: float, world: int) -> float:
+    """Whole-job Gsegments/s: every rank renders its own batch of the same
+    shape (weak scaling), timed by the slowest rank."""
+    return world * segments_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
     """The oracle as it stands, on a bounded random sample of the batch's rays."""
     import oracle
@@ -336,10 +351,8 @@ def run_ours(args):
     ms32 = float(np.mean(t32))
     ms64 = float(np.mean(t64))
     if world > 1:
-        x = torch.tensor([ms32], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        ms32 = float(x.item())
-    value = world * segs / (ms32 * 1e-3) / 1e9
+        ms32 = max_over_ranks(ms32, dev)
+    value = replica_throughput(segs, ms32, world)
     value64 = segs / (ms64 * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: camera upload and map/count readback inside

@@ -325,3 +325,32 @@ def test_graph_replay_matches_direct_launches(gpu):
             assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
         st = r.stats()
         assert st["graph_launches"] >= 21 and 1 <= st["graph_captures"] <= 10
+
+
+def test_sortlast_domains_rendered_in_turn(gpu):
+    """Sec. 3.1 sort-last: partial maps of 3 leaf domains, rendered one after
+    another on the GPU, merge into the whole-tree GPU render."""
+    from paper_1210_8014_gb300 import sortlast
+    tree = tree_of("galaxy")
+    own = sortlast.domain_owner(tree, 3)
+    cams = [c.with_(precision=amr.AMR_PREC_FP32_KAHAN) for c in mixed_batch(tree, 6, seed=31)]
+    with amr.Renderer(tree) as r:
+        whole = [(host(m), host(c)) for m, c in r.render_batch(cams)]
+    parts = {q: [] for q in range(len(cams))}
+    counts = {q: [] for q in range(len(cams))}
+    for d in range(3):
+        for mom in (False, True):
+            sub = [q for q, c in enumerate(cams) if (c.mode == 1) == mom]
+            if not sub:
+                continue
+            with amr.Renderer(sortlast.domain_tree(tree, own, d, with_momentum=mom)) as r:
+                for q in sub:
+                    pcs = sortlast.partial_cameras(cams[q])
+                    outs = r.render_batch(pcs)
+                    parts[q].append([host(m) for m, _ in outs])
+                    counts[q].append(host(outs[0][1]))
+    for q, cam in enumerate(cams):
+        merged, mc = sortlast.merge(cam, parts[q], counts[q])
+        wm, wc = whole[q]
+        assert (mc == wc).all()
+        assert_parity(cam.mode, 1, merged, mc, wm.astype(np.float64), wc, ctx=f"sort-last camera {q}")
