@@ -161,22 +161,39 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   };
 
   // Exact pairwise order of the current cell's exit times t_x = n_x / |D_x|:
-  //   e_xy = n_x |D_y| - n_y |D_x|   (sign of t_x - t_y),
+  //   e_xy = n_x |D_y| - n_y |D_x|   (the sign of t_x - t_y),
   // with n_x the distance (2^-36 units) from the origin to the cell's exit
   // plane on axis x (n = 1, |D| = 0 for an axis the ray runs parallel to,
-  // which makes its time compare as infinite).  sD_x = |D_x| * cell size.
-  long long e01, e02, e12, sD0, sD1, sD2;
+  // which makes its time compare as infinite).  Inside a cell of size s both
+  // exit times lie within s / |D| of the entry time, so |e_xy| <= s * 2^23:
+  // e = E s + r with 0 <= r < s, E a 32-bit integer, and r fixed while the
+  // level holds (a step adds |D| s).  The loop keeps F = 2E + (r > 0): its
+  // sign is the sign of e (F == 0 exactly when e == 0), a step adds 2|D|, and
+  // E = F >> 1.
+  int F01, F02, F12;
+  const int A0 = 2 * aD[0], A1 = 2 * aD[1], A2 = 2 * aD[2];
+  long long r01 = 0, r02 = 0, r12 = 0;                  // remainders (FP64 chords)
+  float q01 = 0, q02 = 0, q12 = 0, p01 = 0, p02 = 0, p12 = 0;  // r and s - r as floats
+  float sf = 0.0f;                                      // s as a float
   auto recompute = [&]() {
     const int sh = kFixBits - lvl;
     const long long n0 = D[0] > 0 ? ((long long)(k0 + 1) << sh) - X[0] : (D[0] < 0 ? X[0] - ((long long)k0 << sh) : 1);
     const long long n1 = D[1] > 0 ? ((long long)(k1 + 1) << sh) - X[1] : (D[1] < 0 ? X[1] - ((long long)k1 << sh) : 1);
     const long long n2 = D[2] > 0 ? ((long long)(k2 + 1) << sh) - X[2] : (D[2] < 0 ? X[2] - ((long long)k2 << sh) : 1);
-    e01 = n0 * aD[1] - n1 * aD[0];
-    e02 = n0 * aD[2] - n2 * aD[0];
-    e12 = n1 * aD[2] - n2 * aD[1];
-    sD0 = (long long)aD[0] << sh;
-    sD1 = (long long)aD[1] << sh;
-    sD2 = (long long)aD[2] << sh;
+    const long long e01 = n0 * aD[1] - n1 * aD[0];
+    const long long e02 = n0 * aD[2] - n2 * aD[0];
+    const long long e12 = n1 * aD[2] - n2 * aD[1];
+    const long long E01 = e01 >> sh, E02 = e02 >> sh, E12 = e12 >> sh;  // floor division by s
+    r01 = e01 - (E01 << sh);
+    r02 = e02 - (E02 << sh);
+    r12 = e12 - (E12 << sh);
+    F01 = 2 * (int)E01 + (r01 != 0);
+    F02 = 2 * (int)E02 + (r02 != 0);
+    F12 = 2 * (int)E12 + (r12 != 0);
+    const long long s = 1LL << sh;
+    q01 = __ll2float_rn(r01); q02 = __ll2float_rn(r02); q12 = __ll2float_rn(r12);
+    p01 = __ll2float_rn(s - r01); p02 = __ll2float_rn(s - r02); p12 = __ll2float_rn(s - r12);
+    sf = __int_as_float((127 + sh) << 23);
   };
 
   descend(1, 0, 0, 0, 0);
@@ -192,9 +209,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     const F rho = load_field<F>(rho_base, cell);
 
     // Exit face(s): the axes whose exit time is the minimum.
-    const bool lt01 = e01 < 0, gt01 = e01 > 0;
-    const bool lt02 = e02 < 0, gt02 = e02 > 0;
-    const bool lt12 = e12 < 0, gt12 = e12 > 0;
+    const bool lt01 = F01 < 0, gt01 = F01 > 0;
+    const bool lt02 = F02 < 0, gt02 = F02 > 0;
+    const bool lt12 = F12 < 0, gt12 = F12 > 0;
     const bool st0 = !gt01 && !gt02;
     const bool st1 = !lt01 && !gt12;
     const bool st2 = !lt02 && !lt12;
@@ -204,14 +221,22 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       if (PREC == AMR_PREC_FP64) Md = fmax(Md, (double)rho);
       else Mf = fmaxf(Mf, (float)rho);
     } else {
-      // Chord.  The cell was entered on its face on axis ea, at n_ea - size, so
-      //   (t_exit - t_entry) |D_ea| |D_b| = sD_b - (n_ea |D_b| - n_b |D_ea|)   (b != ea)
-      //   (t_exit - t_entry) = size / |D_b|                                     (b == ea)
+      // Chord.  The cell was entered through its face on axis ea, at n_ea - s:
+      //   (t_exit - t_entry) |D_ea| |D_b| = s |D_b| - e'   (b != ea),
+      // e' = n_ea |D_b| - n_b |D_ea| = +-e of the pair.  With e = E s + r this is
+      //   (K - 1) s + (s - r),  K = |D_b| - E,  when ea < b  (e' = e),
+      //    K s + r,             K = |D_b| + E,  when ea > b  (e' = -e),
+      // two non-negative parts (K >= 1, resp. K >= 0, since the chord is > 0).
+      //   (t_exit - t_entry) = s / |D_b|                      (b == ea)
       const int pair = ea + b - 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
-      const long long ep = sel3(pair, e01, e02, e12);
-      const long long num = sel3(b, sD0, sD1, sD2) - (ea < b ? ep : -ep);
-      const int e2 = kFixBits - lvl;  // size = 2^e2
+      const bool up = ea < b;
+      const int E = sel3(pair, F01, F02, F12) >> 1;
+      const int aDb = sel3(b, aD[0], aD[1], aD[2]);
+      const int K = up ? aDb - E - 1 : aDb + E;
+      const int e2 = kFixBits - lvl;  // s = 2^e2
       if (PREC == AMR_PREC_FP64) {
+        const long long rp = sel3(pair, r01, r02, r12);
+        const long long num = ((long long)K << e2) + (up ? (1LL << e2) - rp : rp);
         const double lb = cam.lamInv[b];
         const double len = (b == ea) ? lb * __longlong_as_double((long long)(1023 + e2) << 52)
                                      : (double)num * (cam.lamInv[ea] * cam.invD[b]);
@@ -223,9 +248,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           Nd += wgt * vlos;
         }
       } else {
+        // K s is exact in float (|K| < 2^24, s a power of two); one rounding adds the remainder part.
+        const float rest = up ? sel3(pair, p01, p02, p12) : sel3(pair, q01, q02, q12);
+        const float numf = __fmaf_rn(__int2float_rn(K), sf, rest);
         const float lb = sel3(b, lf0, lf1, lf2);
-        const float len = (b == ea) ? __fmul_rn(lb, __int_as_float((127 + e2) << 23))
-                                    : __fmul_rn(__ll2float_rn(num), __fmul_rn(sel3(ea, lf0, lf1, lf2), sel3(b, if0, if1, if2)));
+        const float len = (b == ea) ? __fmul_rn(lb, sf)
+                                    : __fmul_rn(numf, __fmul_rn(sel3(ea, lf0, lf1, lf2), sel3(b, if0, if1, if2)));
         const float wgt = __fmul_rn((float)rho, len);
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
@@ -242,9 +270,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     ea = b;
 
     // Exit planes of the stepped axes move one cell on (valid while the level holds).
-    if (st0) { e01 += sD1; e02 += sD2; }
-    if (st1) { e01 -= sD0; e12 += sD2; }
-    if (st2) { e02 -= sD0; e12 -= sD1; }
+    if (st0) { F01 += A1; F02 += A2; }
+    if (st1) { F01 -= A0; F12 += A2; }
+    if (st2) { F02 -= A0; F12 -= A1; }
     const int stepbits = (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
     const int lvl0 = lvl;
     if (NB) {
