@@ -137,6 +137,19 @@ amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_
 amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
                             int32_t* const* counts, int out_on_device, void* cuda_stream);
 
+/*
+ * Slice map (Sec. 3.3: the "Slicemap" tree search the authors moved to the
+ * GPU): for each pixel centre — the plane through cam->centre spanned by u, v,
+ * the same pixel lattice and quantisation as the rays — the value of
+ * cam->field_value in the leaf holding that point at the camera's level cut
+ * (half-open cells).  map_out: double [ny][nx] for AMR_PREC_FP64, else float;
+ * level_out (nullable): int32 [ny][nx], the level of that leaf, 0 where the
+ * point lies outside the box (the value there is 0).  cam->mode is ignored.
+ * Pointers and stream as in amr_render.
+ */
+amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* level_out, int out_on_device,
+                     void* cuda_stream);
+
 /* Validate a camera against the loaded tree; *level_out (nullable) receives the
  * level cut it renders at. */
 amr_status amr_camera_check(amr_ctx* ctx, const amr_camera* cam, int32_t* level_out);

@@ -69,6 +69,9 @@ def load(path: Path | None = None):
     lib.oracle_view_info.restype = ctypes.c_int
     lib.oracle_ray_origin.argtypes = [ctypes.POINTER(OracleCamera), ctypes.c_int32, ctypes.c_int32, P]
     lib.oracle_ray_origin.restype = ctypes.c_int
+    lib.oracle_slice.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.POINTER(P),
+                                 ctypes.POINTER(OracleCamera), P, P, ctypes.c_int32]
+    lib.oracle_slice.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -150,3 +153,17 @@ def ray_origin(cam, i, j, lib=None):
     if st != OR_OK:
         raise ValueError(f"oracle_ray_origin failed ({st})")
     return X0
+
+
+def slice_map(tree, cam, threads: int = 0, lib=None):
+    """Slice map: (values float64 [ny, nx], leaf levels int32 [ny, nx])."""
+    lib = lib or load()
+    t = prepare(tree)
+    c = to_camera(cam)
+    out = np.zeros((int(cam.ny), int(cam.nx)), np.float64)
+    lv = np.zeros((int(cam.ny), int(cam.nx)), np.int32)
+    st = lib.oracle_slice(t.level.shape[0], t.level.ctypes.data, t.coord.ctypes.data, t.child.ctypes.data,
+                          len(t.fields), t.ptrs, ctypes.byref(c), out.ctypes.data, lv.ctypes.data, threads)
+    if st != OR_OK:
+        raise ValueError(f"oracle_slice failed ({st})")
+    return out, lv

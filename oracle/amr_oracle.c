@@ -125,6 +125,18 @@ static void pixel_centre(const oracle_camera* cam, int i, int j, double x[3]) {
   }
 }
 
+/* The quantised pixel centre X0 = round-half-even(x 2^36); 1 if x leaves [-1, 2]^3. */
+static int quantised_origin(const oracle_camera* cam, int i, int j, int64_t X0[3]) {
+  double x[3];
+  pixel_centre(cam, i, j, x);
+  int bad = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (!(x[a] >= -1.0 && x[a] <= 2.0)) bad = 1;
+    X0[a] = bad ? 0 : llrint(ldexp(x[a], OR_K));
+  }
+  return bad;
+}
+
 /* An event: the ray parameter t = num / den with den = |D_axis| > 0. */
 typedef struct {
   i128 num, den;
@@ -302,14 +314,8 @@ int oracle_render(int64_t n_oct, const uint8_t* level, const int32_t* coord, con
   for (int64_t q = 0; q < total; ++q) {
     int i = n_pix >= 0 ? pix_i[q] : (int)(q % cam->nx);
     int j = n_pix >= 0 ? pix_j[q] : (int)(q / cam->nx);
-    double x[3];
-    pixel_centre(cam, i, j, x);
     int64_t X0[3];
-    int bad = 0;
-    for (int a = 0; a < 3; ++a) {
-      if (!(x[a] >= -1.0 && x[a] <= 2.0)) bad = 1;
-      X0[a] = bad ? 0 : llrint(ldexp(x[a], OR_K));
-    }
+    int bad = quantised_origin(cam, i, j, X0);
     int s = bad ? OR_E_INVALID : cast_ray(&tr, cam, &vw, X0, &map[q], &counts[q]);
     if (s != OR_OK) {
 #ifdef _OPENMP
@@ -335,11 +341,66 @@ int oracle_view_info(int64_t n_oct, const uint8_t* level, const oracle_camera* c
 
 /* The quantised origin of pixel (i, j): X0[3]. */
 int oracle_ray_origin(const oracle_camera* cam, int32_t i, int32_t j, int64_t* X0) {
-  double x[3];
-  pixel_centre(cam, i, j, x);
-  for (int a = 0; a < 3; ++a) {
-    if (!(x[a] >= -1.0 && x[a] <= 2.0)) return OR_E_INVALID;
-    X0[a] = llrint(ldexp(x[a], OR_K));
+  return quantised_origin(cam, i, j, X0) ? OR_E_INVALID : OR_OK;
+}
+
+/*
+ * Slice map (Sec. 3.3, "Slicemap", a tree search): for each pixel centre (on
+ * the plane through the camera centre spanned by u and v), the value of the
+ * leaf containing that point at the camera's level cut, and that leaf's level
+ * (0 and 0 outside the box).  Containment is half-open: the point belongs to
+ * the cell whose low faces it lies on.  The descent compares the quantised
+ * point with each oct's mid-planes, taken from the coord array.
+ */
+int oracle_slice(int64_t n_oct, const uint8_t* level, const int32_t* coord, const int32_t* child,
+                 int32_t n_fields, const double* const* fields, const oracle_camera* cam, double* map,
+                 int32_t* levels, int32_t n_threads) {
+  if (n_oct < 1 || !level || !coord || !child || !fields || !cam || !map || !levels) return OR_E_INVALID;
+  if (cam->field_value < 0 || cam->field_value >= n_fields) return OR_E_INVALID;
+  oracle_view vw;
+  int st = make_view(cam, tree_depth(n_oct, level), &vw);
+  if (st != OR_OK) return st;
+  const int64_t box = (int64_t)1 << OR_K;
+  const double* f = fields[cam->field_value];
+  int64_t total = (int64_t)cam->nx * cam->ny;
+  int err = OR_OK;
+#ifdef _OPENMP
+  int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nt)
+#endif
+  for (int64_t q = 0; q < total; ++q) {
+    int64_t X0[3];
+    int bad = quantised_origin(cam, (int)(q % cam->nx), (int)(q / cam->nx), X0);
+    int inside = 1;
+    for (int a = 0; a < 3; ++a)
+      if (!(X0[a] >= 0 && X0[a] < box)) inside = 0;
+    map[q] = 0.0;
+    levels[q] = 0;
+    if (bad) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      err = OR_E_INVALID;
+      continue;
+    }
+    if (!inside) continue;
+    int64_t oct = 0;
+    int lvl = 1;
+    for (;;) {
+      int c = 0;
+      for (int b = 0; b < 3; ++b) {
+        int64_t mid = ((int64_t)coord[3 * oct + b] + 1) << (OR_K - lvl);
+        c |= (X0[b] >= mid) << b;
+      }
+      int32_t ch = child[8 * oct + c];
+      if (ch < 0 || lvl == vw.L) {
+        map[q] = f[8 * oct + c];
+        levels[q] = lvl;
+        break;
+      }
+      oct = ch;
+      ++lvl;
+    }
   }
-  return OR_OK;
+  return err;
 }

@@ -112,3 +112,22 @@ def bruteforce(tree, cam, pixels=None):
         else:
             out[q] = float(np.max(fld[cam.field_value][hit])) if cnt[q] else 0.0
     return out.reshape(shape), cnt.reshape(shape)
+
+
+def bruteforce_slice(tree, cam):
+    """Slice map by scanning every render leaf for the one containing each
+    quantised pixel centre (half-open cells)."""
+    L = cut_level(cam, int(tree.level.max()))
+    o, c, lvl, lo, hi = render_leaves(tree, L)
+    vals = np.asarray(tree.fields[cam.field_value], np.float64)[o, c]
+    out = np.zeros((cam.ny, cam.nx), np.float64)
+    lv = np.zeros((cam.ny, cam.nx), np.int32)
+    for j in range(cam.ny):
+        for i in range(cam.nx):
+            X0 = origin(cam, i, j)
+            hit = np.nonzero(((lo <= X0) & (X0 < hi)).all(axis=1))[0]
+            if hit.size:
+                assert hit.size == 1
+                out[j, i] = vals[hit[0]]
+                lv[j, i] = lvl[hit[0]]
+    return out, lv

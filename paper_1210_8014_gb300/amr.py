@@ -69,6 +69,7 @@ def lib():
             "amr_render_batch": [P, I32, ctypes.POINTER(amr_camera), ctypes.POINTER(P), ctypes.POINTER(P),
                                  ctypes.c_int, P],
             "amr_camera_check": [P, ctypes.POINTER(amr_camera), ctypes.POINTER(I32)],
+            "amr_slice": [P, ctypes.POINTER(amr_camera), P, P, ctypes.c_int, P],
             "amr_set_options": [P, ctypes.POINTER(amr_options)],
             "amr_get_options": [P, ctypes.POINTER(amr_options)],
             "amr_autotune": [P, I32, ctypes.POINTER(amr_camera), I32, ctypes.POINTER(amr_options),
@@ -156,6 +157,12 @@ def amr_render_batch(ctx, cams: Sequence[Camera], maps: Sequence, counts: Option
     karr = (ctypes.c_void_p * n)(*[_ptr(k) for k in counts]) if counts is not None else None
     _check(lib().amr_render_batch(ctx, n, carr, marr, karr, int(out_on_device),
                                   _ptr(cuda_stream) if cuda_stream is not None else None))
+
+
+def amr_slice(ctx, cam: Camera, map_out, level_out=None, out_on_device: int = 1, cuda_stream=None) -> None:
+    c = to_camera(cam)
+    _check(lib().amr_slice(ctx, ctypes.byref(c), _ptr(map_out), _ptr(level_out), int(out_on_device),
+                           _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 def amr_camera_check(ctx, cam: Camera) -> int:
@@ -277,6 +284,12 @@ class Renderer:
         amr_render_batch(self.ctx, cams, [o[0] for o in outs], [o[1] for o in outs] if with_counts else None, 1,
                          s.cuda_stream)
         return outs
+
+    def slice(self, cam: Camera, stream=None):
+        m, c = self.alloc(cam)
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        amr_slice(self.ctx, cam, m, c, 1, s.cuda_stream)
+        return m, c
 
     def stats(self) -> dict:
         return amr_stats(self.ctx)

@@ -451,6 +451,31 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   return AMR_OK;
 }
 
+// One slice-map launch through a launch slot (the camera record and error word
+// live in the slot's scratch, so back-to-back calls on any stream do not race).
+amr_status enqueue_slice(amr_ctx* ctx, const CamDev& cam, bool out64, cudaStream_t stream, LaunchSlot** used) {
+  std::unique_lock<std::mutex> lk(ctx->launch_mu);
+  LaunchSlot& s = ctx->slots[ctx->next_slot];
+  ctx->next_slot = (ctx->next_slot + 1) % ctx->slots.size();
+  if (s.pending) {
+    CUDA_TRY(cudaEventSynchronize(s.done));
+    harvest(ctx, s);
+  }
+  s.h_cams[0] = cam;
+  s.n_groups = amr::kMaxPrecisions;
+  CUDA_TRY(cudaEventRecord(s.start, stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_cams, s.h_cams, sizeof(CamDev), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), stream));
+  CUDA_TRY(amr::launch_slice(out64, ctx->tree.f64, ctx->tree.rec, (uint32_t)ctx->tree.n_oct, s.d_cams,
+                             (int64_t)cam.nx * cam.ny, &s.d_q[0].error, stream));
+  CUDA_TRY(cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaEventRecord(s.done, stream));
+  s.pending = true;
+  ctx->n_renders++;
+  if (used) *used = &s;
+  return AMR_OK;
+}
+
 amr_status finish_sync(amr_ctx* ctx, LaunchSlot* s) {
   CUDA_TRY(cudaEventSynchronize(s->done));
   std::lock_guard<std::mutex> lk(ctx->launch_mu);
@@ -912,6 +937,38 @@ amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_
 amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
                             int32_t* const* counts, int out_on_device, void* cuda_stream) {
   return render_impl(ctx, n, cams, maps, counts, out_on_device, cuda_stream);
+}
+
+amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* level_out, int out_on_device,
+                     void* cuda_stream) {
+  if (!ctx || !cam || !map_out) return fail(AMR_E_INVALID, "null argument");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  amr_camera c = *cam;
+  c.mode = AMR_MODE_COLUMN;  // the slice reads field_value only
+  CamDev d;
+  amr_status st = canonicalise(ctx, c, ctx->opt.tile_w, ctx->opt.tile_h, d);
+  if (st != AMR_OK) return st;
+  const bool out64 = cam->precision == AMR_PREC_FP64;
+  const int64_t px = (int64_t)c.nx * c.ny;
+  const int64_t mbytes = px * (out64 ? 8 : 4);
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  LaunchSlot* s = nullptr;
+  if (out_on_device) {
+    d.map = map_out;
+    d.counts = level_out;
+    return enqueue_slice(ctx, d, out64, stream, &s);
+  }
+  const int64_t moff = ((mbytes + 255) / 256) * 256;
+  st = ensure_stage(ctx, moff + (level_out ? px * 4 : 0));
+  if (st != AMR_OK) return st;
+  d.map = ctx->stage;
+  d.counts = level_out ? (int32_t*)((char*)ctx->stage + moff) : nullptr;
+  st = enqueue_slice(ctx, d, out64, stream, &s);
+  if (st != AMR_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(map_out, d.map, (size_t)mbytes, cudaMemcpyDeviceToHost, stream));
+  if (level_out) CUDA_TRY(cudaMemcpyAsync(level_out, d.counts, (size_t)px * 4, cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  return finish_sync(ctx, s);
 }
 
 amr_status amr_camera_check(amr_ctx* ctx, const amr_camera* cam, int32_t* level_out) {

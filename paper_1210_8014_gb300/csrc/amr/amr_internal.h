@@ -73,6 +73,10 @@ int32_t set_error(int32_t st, const char* msg);
 
 // Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is double.
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s);
+// Slice map of one camera (cam: a device CamDev whose map/counts point to the
+// outputs; out64: double map).  err: device int set to 1 on a bad oct index.
+cudaError_t launch_slice(bool out64, bool f64, const uint2* rec, uint32_t n_oct, const CamDev* cam, int64_t n_px,
+                         int32_t* err, cudaStream_t s);
 // Largest resident blocks per SM for the kernel of (prec, f64, with neighbour
 // links) at this block size.
 cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm);

@@ -279,3 +279,27 @@ def pin_quantisation(lib):
 
 ALL_PINS = [pin_golden, pin_quantisation, pin_uniform_axis, pin_uniform_oblique, pin_single_leaf,
             pin_bruteforce, pin_mass, pin_split, pin_symmetry, pin_sortlast, pin_wmean_constant, pin_level_rule]
+
+
+def pin_slice(lib):
+    """Slice map: golden points of the two-level tree, and brute-force containment."""
+    tree, _ = golden_tree()
+    # pixel centres x, y in {0.125, 0.375} on the plane z = 0.25, the low face of
+    # level-2 z-index 1: the cells with z-bit 1 of the refined oct in root cell 0
+    cam = inputs.Camera((0.25, 0.25, 0.25), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (0.5, 0.5), 2, 2,
+                        max_level=2)
+    m, lv = oracle.slice_map(tree, cam, lib=lib)
+    assert m.tolist() == [[14.0, 15.0], [16.0, 17.0]] and (lv == 2).all(), (m, lv)
+    m1, lv1 = oracle.slice_map(tree, cam.with_(max_level=1), lib=lib)
+    assert (m1 == 13.5).all() and (lv1 == 1).all()
+    rng = np.random.default_rng(99)
+    for k in range(3):
+        t = inputs.random_tree(rng, depth=4, p_refine=0.4)
+        c = inputs.camera_along(inputs.random_direction(rng), centre=rng.uniform(0.2, 0.8, 3), fov=1.4, n=9,
+                                max_level=int(rng.integers(1, 5)))
+        m, lv = oracle.slice_map(t, c, lib=lib)
+        bm, blv = bf.bruteforce_slice(t, c)
+        assert (m == bm).all() and (lv == blv).all(), k
+
+
+ALL_PINS.append(pin_slice)

@@ -34,6 +34,8 @@ MUTANTS = {
     "origin_truncated": ("X0[a] = bad ? 0 : llrint(ldexp(x[a], OR_K));", "X0[a] = bad ? 0 : (int64_t)(ldexp(x[a], OR_K));"),
     "value_from_sibling_cell": ("double r = rho[8 * oct + c];", "double r = rho[8 * oct + (c ^ 1)];"),
     "exit_uses_lower_face_going_up": ("(i128)(k + 1) * size - X0[b]", "(i128)k * size - X0[b]"),
+    "slice_point_on_face_goes_low": ("c |= (X0[b] >= mid) << b;", "c |= (X0[b] > mid) << b;"),
+    "slice_ignores_cut": ("if (ch < 0 || lvl == vw.L) {", "if (ch < 0) {"),
 }
 
 
