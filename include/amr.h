@@ -52,7 +52,7 @@ enum {
 };
 
 enum { AMR_F32 = 0, AMR_F64 = 1 };
-enum { AMR_MODE_COLUMN = 0, AMR_MODE_WMEAN = 1, AMR_MODE_MAX = 2 };
+enum { AMR_MODE_COLUMN = 0, AMR_MODE_WMEAN = 1, AMR_MODE_MAX = 2, AMR_MODE_LEVEL = 3 };
 enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32_KAHAN = 1, AMR_PREC_FP32_PLAIN = 2 };
 #define AMR_LEVEL_AUTO (-1)   /* deepest level whose cell edge is at least one pixel */
 
@@ -68,6 +68,9 @@ enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32_KAHAN = 1, AMR_PREC_FP32_PLAIN = 2 };
  *   mode            : AMR_MODE_COLUMN  sum rho*len over crossed leaves
  *                     AMR_MODE_WMEAN   sum rho*(v.w)*len / sum rho*len (0 if empty)
  *                     AMR_MODE_MAX     max rho over crossed leaves (0 if empty)
+ *                     AMR_MODE_LEVEL   sum rho*len*level / sum rho*len: the
+ *                                      local mesh resolution that amr_blur follows
+ *                                      (rho from field_weight; 0 if empty)
  *   precision       : AMR_PREC_FP64 (plain double sums, double map);
  *                     AMR_PREC_FP32_KAHAN (float chords, compensated float sums,
  *                     float map); AMR_PREC_FP32_PLAIN (uncompensated float sums).
@@ -149,6 +152,21 @@ amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, voi
  */
 amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* level_out, int out_on_device,
                      void* cuda_stream);
+
+/*
+ * Adaptive Gaussian blur (Sec. 2.2: the post-process that follows the local
+ * image resolution, against the aliasing of coarse cells).  in, level, out:
+ * device float [ny][nx]; level is the AMR_MODE_LEVEL map of the same camera;
+ * pixel is the pixel edge in box units (fov[0] / nx).  Per pixel, sigma =
+ * 2^-level / (2 pixel) pixels (below 0.5: copied unchanged); separable, rows
+ * then columns, each output pixel with its own sigma; weights
+ * exp(-k^2 / (2 sigma^2)), |k| <= floor(3 sigma + 0.5) capped at 64, renormalised
+ * over the samples inside the map.  in and out may not alias.  Enqueued on
+ * cuda_stream; the intermediate buffer belongs to the context (one blur at a
+ * time per context).
+ */
+amr_status amr_blur(amr_ctx* ctx, int32_t nx, int32_t ny, const float* in, const float* level, double pixel,
+                    float* out, void* cuda_stream);
 
 /* Validate a camera against the loaded tree; *level_out (nullable) receives the
  * level cut it renders at. */

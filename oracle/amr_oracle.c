@@ -15,6 +15,8 @@
  *     column : S = sum rho_i * len_i
  *     wmean  : sum rho_i * vlos_i * len_i / sum rho_i * len_i   (0 if empty)
  *     max    : max rho_i over crossed leaves (MIP maps, Sec. 2.1)
+ *     level  : sum rho_i * len_i * level_i / sum rho_i * len_i, the local mesh
+ *              resolution an adaptive blur follows (Sec. 2.2)
  *   and the number of leaves crossed with positive length.
  *
  * Readings where the paper is silent (each also listed in the design notes):
@@ -53,7 +55,7 @@
 typedef __int128 i128;
 
 enum { OR_OK = 0, OR_E_INVALID = -1, OR_E_BADTREE = -2 };
-enum { OR_COLUMN = 0, OR_WMEAN = 1, OR_MAX = 2 };
+enum { OR_COLUMN = 0, OR_WMEAN = 1, OR_MAX = 2, OR_LEVEL = 3 };
 
 #define OR_K 36          /* fixed-point bits of a coordinate (level 22 + 14 guard bits) */
 #define OR_DBITS 23      /* bits of the largest direction component */
@@ -86,7 +88,7 @@ static int tree_depth(int64_t n_oct, const uint8_t* level) {
 /* Camera set-up (Sec. 2: the camera defines the deepest level). */
 static int make_view(const oracle_camera* cam, int depth, oracle_view* vw) {
   if (cam->nx <= 0 || cam->ny <= 0) return OR_E_INVALID;
-  if (cam->mode < OR_COLUMN || cam->mode > OR_MAX) return OR_E_INVALID;
+  if (cam->mode < OR_COLUMN || cam->mode > OR_LEVEL) return OR_E_INVALID;
   if (!(cam->fov[0] > 0.0) || !(cam->fov[1] > 0.0)) return OR_E_INVALID;
   const double tol = 1e-9;
   if (fabs(dot3(cam->u, cam->u) - 1.0) > tol || fabs(dot3(cam->v, cam->v) - 1.0) > tol ||
@@ -213,7 +215,8 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
   }
   if (time_cmp(tin, tout) >= 0) return OR_OK; /* misses the box, or touches it with zero length */
 
-  const double* rho = tr->fields[cam->mode == OR_WMEAN ? cam->field_weight : cam->field_value];
+  const int weighted = cam->mode == OR_WMEAN || cam->mode == OR_LEVEL;
+  const double* rho = tr->fields[weighted ? cam->field_weight : cam->field_value];
   nsum S = {0, 0}, N = {0, 0};
   double M = 0.0;
   int32_t cnt = 0;
@@ -262,6 +265,9 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
                     tr->fields[cam->field_vel[2]][8 * oct + c] * cam->w[2];
       nadd(&S, r * len);
       nadd(&N, r * vlos * len);
+    } else if (cam->mode == OR_LEVEL) {
+      nadd(&S, r * len);
+      nadd(&N, r * len * (double)lvl);
     } else {
       if (cnt == 0 || r > M) M = r;
     }
@@ -271,7 +277,7 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
   }
   if (cam->mode == OR_COLUMN) {
     *out = S.s + S.c;
-  } else if (cam->mode == OR_WMEAN) {
+  } else if (cam->mode == OR_WMEAN || cam->mode == OR_LEVEL) {
     double s = S.s + S.c;
     *out = s != 0.0 ? (N.s + N.c) / s : 0.0;
   } else {
@@ -284,6 +290,7 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
 static int field_ok(int32_t f, int32_t n_fields) { return f >= 0 && f < n_fields; }
 
 static int fields_ok(const oracle_camera* cam, int32_t n_fields) {
+  if (cam->mode == OR_LEVEL) return field_ok(cam->field_weight, n_fields);
   if (cam->mode != OR_WMEAN) return field_ok(cam->field_value, n_fields);
   return field_ok(cam->field_weight, n_fields) && field_ok(cam->field_vel[0], n_fields) &&
          field_ok(cam->field_vel[1], n_fields) && field_ok(cam->field_vel[2], n_fields);

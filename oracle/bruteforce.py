@@ -63,7 +63,7 @@ def bruteforce(tree, cam, pixels=None):
     D = quantised_direction(cam)
     aD = np.abs(D)
     lam = np.sqrt(np.longdouble(int((D * D).sum()))) / np.longdouble(2.0 ** K)
-    o, c, _, lo, hi = render_leaves(tree, L)
+    o, c, lvls, lo, hi = render_leaves(tree, L)
     fld = [np.asarray(f, np.float64)[o, c].astype(np.longdouble) for f in tree.fields]
     w = np.asarray(cam.w, np.float64)
     if pixels is None:
@@ -109,6 +109,10 @@ def bruteforce(tree, cam, pixels=None):
                     + fld[cam.field_vel[2]][hit] * np.longdouble(w[2]))
             S = np.sum(rho * ln)
             out[q] = float(np.sum(rho * vlos * ln) / S) if S != 0 else 0.0
+        elif cam.mode == 3:
+            rho = fld[cam.field_weight][hit]
+            S = np.sum(rho * ln)
+            out[q] = float(np.sum(rho * ln * lvls[hit].astype(np.longdouble)) / S) if S != 0 else 0.0
         else:
             out[q] = float(np.max(fld[cam.field_value][hit])) if cnt[q] else 0.0
     return out.reshape(shape), cnt.reshape(shape)

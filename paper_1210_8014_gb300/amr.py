@@ -21,7 +21,7 @@ from .inputs import Camera, Tree
 AMR_OK, AMR_E_INVALID, AMR_E_BADTREE, AMR_E_OOM, AMR_E_CUDA = 0, -1, -2, -3, -4
 AMR_E_TIMEOUT, AMR_E_BUSY, AMR_E_CANCELLED = -5, -6, -7
 AMR_F32, AMR_F64 = 0, 1
-AMR_MODE_COLUMN, AMR_MODE_WMEAN, AMR_MODE_MAX = 0, 1, 2
+AMR_MODE_COLUMN, AMR_MODE_WMEAN, AMR_MODE_MAX, AMR_MODE_LEVEL = 0, 1, 2, 3
 AMR_PREC_FP64, AMR_PREC_FP32_KAHAN, AMR_PREC_FP32_PLAIN = 0, 1, 2
 AMR_LEVEL_AUTO = -1
 
@@ -70,6 +70,7 @@ def lib():
                                  ctypes.c_int, P],
             "amr_camera_check": [P, ctypes.POINTER(amr_camera), ctypes.POINTER(I32)],
             "amr_slice": [P, ctypes.POINTER(amr_camera), P, P, ctypes.c_int, P],
+            "amr_blur": [P, I32, I32, P, P, ctypes.c_double, P, P],
             "amr_set_options": [P, ctypes.POINTER(amr_options)],
             "amr_get_options": [P, ctypes.POINTER(amr_options)],
             "amr_autotune": [P, I32, ctypes.POINTER(amr_camera), I32, ctypes.POINTER(amr_options),
@@ -163,6 +164,11 @@ def amr_slice(ctx, cam: Camera, map_out, level_out=None, out_on_device: int = 1,
     c = to_camera(cam)
     _check(lib().amr_slice(ctx, ctypes.byref(c), _ptr(map_out), _ptr(level_out), int(out_on_device),
                            _ptr(cuda_stream) if cuda_stream is not None else None))
+
+
+def amr_blur(ctx, nx: int, ny: int, map_in, level, pixel: float, map_out, cuda_stream=None) -> None:
+    _check(lib().amr_blur(ctx, int(nx), int(ny), _ptr(map_in), _ptr(level), float(pixel), _ptr(map_out),
+                          _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 def amr_camera_check(ctx, cam: Camera) -> int:

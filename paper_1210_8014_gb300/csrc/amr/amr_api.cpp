@@ -101,6 +101,8 @@ struct amr_ctx {
   std::mutex launch_mu;  // guards slots and stats
   std::vector<LaunchSlot> slots;
   size_t next_slot = 0;
+  void* blur_tmp = nullptr;  // intermediate of the separable blur
+  int64_t blur_cap = 0;
   void* stage = nullptr;  // device staging for host-output renders
   int64_t stage_cap = 0;
   // stats
@@ -222,7 +224,7 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
   if (!t.loaded) return fail(AMR_E_INVALID, "no octree loaded");
   if (c.nx <= 0 || c.ny <= 0 || (int64_t)c.nx * c.ny >= (int64_t(1) << 31))
     return fail(AMR_E_INVALID, "map size %d x %d out of range", c.nx, c.ny);
-  if (c.mode < AMR_MODE_COLUMN || c.mode > AMR_MODE_MAX) return fail(AMR_E_INVALID, "unknown mode %d", c.mode);
+  if (c.mode < AMR_MODE_COLUMN || c.mode > AMR_MODE_LEVEL) return fail(AMR_E_INVALID, "unknown mode %d", c.mode);
   if (c.precision < AMR_PREC_FP64 || c.precision > AMR_PREC_FP32_PLAIN)
     return fail(AMR_E_INVALID, "unknown precision %d", c.precision);
   const int nf = t.n_fields;
@@ -230,6 +232,8 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
   if (c.mode == AMR_MODE_WMEAN) {
     if (!fok(c.field_weight) || !fok(c.field_vel[0]) || !fok(c.field_vel[1]) || !fok(c.field_vel[2]))
       return fail(AMR_E_INVALID, "wmean needs a weight field and 3 velocity fields (tree has %d fields)", nf);
+  } else if (c.mode == AMR_MODE_LEVEL) {
+    if (!fok(c.field_weight)) return fail(AMR_E_INVALID, "weight field %d out of range", c.field_weight);
   } else if (!fok(c.field_value)) {
     return fail(AMR_E_INVALID, "field %d out of range (tree has %d fields)", c.field_value, nf);
   }
@@ -297,6 +301,8 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
   if (c.mode == AMR_MODE_WMEAN) {
     d.rho = t.fields[c.field_weight];
     for (int a = 0; a < 3; ++a) d.vel[a] = t.fields[c.field_vel[a]];
+  } else if (c.mode == AMR_MODE_LEVEL) {
+    d.rho = t.fields[c.field_weight];
   } else {
     d.rho = t.fields[c.field_value];
   }
@@ -839,6 +845,7 @@ amr_status amr_destroy(amr_ctx* ctx) {
   }
   free_tree(ctx->tree);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->blur_tmp) cudaFree(ctx->blur_tmp);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return AMR_OK;
@@ -969,6 +976,31 @@ amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t
   if (level_out) CUDA_TRY(cudaMemcpyAsync(level_out, d.counts, (size_t)px * 4, cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
   return finish_sync(ctx, s);
+}
+
+amr_status amr_blur(amr_ctx* ctx, int32_t nx, int32_t ny, const float* in, const float* level, double pixel,
+                    float* out, void* cuda_stream) {
+  if (!ctx || !in || !level || !out) return fail(AMR_E_INVALID, "null argument");
+  if (nx <= 0 || ny <= 0 || (int64_t)nx * ny >= (int64_t(1) << 31)) return fail(AMR_E_INVALID, "map size %d x %d", nx, ny);
+  if (!(pixel > 0.0) || !std::isfinite(pixel)) return fail(AMR_E_INVALID, "pixel size must be positive");
+  if (in == out) return fail(AMR_E_INVALID, "in and out alias");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const int64_t bytes = (int64_t)nx * ny * 4;
+  if (ctx->blur_cap < bytes) {
+    if (ctx->blur_tmp) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      cudaFree(ctx->blur_tmp);
+    }
+    ctx->blur_tmp = nullptr;
+    ctx->blur_cap = 0;
+    if (cudaMalloc(&ctx->blur_tmp, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AMR_E_OOM, "blur buffer of %lld bytes", (long long)bytes);
+    }
+    ctx->blur_cap = bytes;
+  }
+  CUDA_TRY(amr::launch_blur(in, level, pixel, (float*)ctx->blur_tmp, out, nx, ny, (cudaStream_t)cuda_stream));
+  return AMR_OK;
 }
 
 amr_status amr_camera_check(amr_ctx* ctx, const amr_camera* cam, int32_t* level_out) {

@@ -77,6 +77,9 @@ cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int b
 // outputs; out64: double map).  err: device int set to 1 on a bad oct index.
 cudaError_t launch_slice(bool out64, bool f64, const uint2* rec, uint32_t n_oct, const CamDev* cam, int64_t n_px,
                          int32_t* err, cudaStream_t s);
+// Adaptive blur: row pass into tmp, column pass into out (device [ny][nx] floats).
+cudaError_t launch_blur(const float* in, const float* level, double pixel, float* tmp, float* out, int nx, int ny,
+                        cudaStream_t s);
 // Largest resident blocks per SM for the kernel of (prec, f64, with neighbour
 // links) at this block size.
 cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm);

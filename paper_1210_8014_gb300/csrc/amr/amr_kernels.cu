@@ -246,6 +246,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           const double vlos = (double)load_field<F>(v0, cell) * cam.w[0] + (double)load_field<F>(v1, cell) * cam.w[1] +
                               (double)load_field<F>(v2, cell) * cam.w[2];
           Nd += wgt * vlos;
+        } else if (MODE == AMR_MODE_LEVEL) {
+          Nd += wgt * (double)lvl;
         }
       } else {
         // K s is exact in float (|K| < 2^24, s a power of two); one rounding adds the remainder part.
@@ -257,9 +259,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         const float wgt = __fmul_rn((float)rho, len);
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
-        if (MODE == AMR_MODE_WMEAN) {
-          const float vlos = (float)load_field<F>(v0, cell) * cam.wF[0] + (float)load_field<F>(v1, cell) * cam.wF[1] +
-                             (float)load_field<F>(v2, cell) * cam.wF[2];
+        if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) {
+          const float vlos = MODE == AMR_MODE_LEVEL
+                                 ? (float)lvl
+                                 : (float)load_field<F>(v0, cell) * cam.wF[0] + (float)load_field<F>(v1, cell) * cam.wF[1] +
+                                       (float)load_field<F>(v2, cell) * cam.wF[2];
           const float nv = __fmul_rn(wgt, vlos);
           if (PREC == AMR_PREC_FP32_KAHAN) neumaier_add(Nf, cNf, nv);
           else Nf = __fadd_rn(Nf, nv);
@@ -384,12 +388,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   res.count = count;
   if (PREC == AMR_PREC_FP64) {
     if (MODE == AMR_MODE_COLUMN) res.d = Sd;
-    else if (MODE == AMR_MODE_WMEAN) res.d = Sd != 0.0 ? Nd / Sd : 0.0;
+    else if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) res.d = Sd != 0.0 ? Nd / Sd : 0.0;
     else res.d = Md;
   } else {
     if (MODE == AMR_MODE_COLUMN) {
       res.f = PREC == AMR_PREC_FP32_KAHAN ? __fsub_rn(Sf, cSf) : Sf;
-    } else if (MODE == AMR_MODE_WMEAN) {
+    } else if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) {
       const float S = PREC == AMR_PREC_FP32_KAHAN ? __fsub_rn(Sf, cSf) : Sf;
       const float N = PREC == AMR_PREC_FP32_KAHAN ? __fadd_rn(Nf, cNf) : Nf;
       res.f = S != 0.0f ? __fdiv_rn(N, S) : 0.0f;
@@ -406,6 +410,7 @@ __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& ca
   switch (cam.mode) {
     case AMR_MODE_COLUMN: o = trace_ray<PREC, AMR_MODE_COLUMN, NB, F>(A, cam, i, j); break;
     case AMR_MODE_WMEAN: o = trace_ray<PREC, AMR_MODE_WMEAN, NB, F>(A, cam, i, j); break;
+    case AMR_MODE_LEVEL: o = trace_ray<PREC, AMR_MODE_LEVEL, NB, F>(A, cam, i, j); break;
     default: o = trace_ray<PREC, AMR_MODE_MAX, NB, F>(A, cam, i, j); break;
   }
   const size_t px = (size_t)j * cam.nx + i;

@@ -26,10 +26,10 @@ import numpy as np
 
 from . import _build
 
-MODE_COLUMN, MODE_WMEAN, MODE_MAX = 0, 1, 2
+MODE_COLUMN, MODE_WMEAN, MODE_MAX, MODE_LEVEL = 0, 1, 2, 3
 PREC_FP64, PREC_FP32_KAHAN, PREC_FP32_PLAIN = 0, 1, 2
 LEVEL_AUTO = -1
-MODE_NAMES = {MODE_COLUMN: "column", MODE_WMEAN: "wmean", MODE_MAX: "max"}
+MODE_NAMES = {MODE_COLUMN: "column", MODE_WMEAN: "wmean", MODE_MAX: "max", MODE_LEVEL: "level"}
 PREC_NAMES = {PREC_FP64: "fp64", PREC_FP32_KAHAN: "fp32_kahan", PREC_FP32_PLAIN: "fp32_plain"}
 
 

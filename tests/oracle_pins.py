@@ -137,7 +137,7 @@ def _bruteforce_cases():
                 w = inputs.random_direction(rng)
             L = int(rng.integers(2, 6)) if k > 3 else -1
             cam = inputs.camera_along(w, centre=(0.5, 0.5, 0.5), fov=(1.0, 0.75), n=(16, 12), max_level=L)
-        for mode in (0, 1, 2):
+        for mode in (0, 1, 2, 3):
             cases.append((tree, cam.with_(mode=mode)))
     return cases
 
@@ -151,7 +151,7 @@ def pin_bruteforce(lib):
             err = np.abs(m - bm) / np.maximum(np.abs(bm), 1e-300)
             err[bm == 0] = np.abs(m[bm == 0])
             assert err.max() <= 1e-14, ("column", err.max())
-        elif cam.mode == 1:
+        elif cam.mode in (1, 3):
             assert np.abs(m - bm).max() <= 1e-13 * max(1e-300, np.abs(bm).max()), ("wmean", np.abs(m - bm).max())
         else:
             assert (m == bm).all(), "max"
@@ -243,6 +243,16 @@ def pin_wmean_constant(lib):
         assert (m[c == 0] == 0).all()
 
 
+def pin_mean_level_uniform(lib):
+    """A complete tree gives mean level = the cut level exactly, at every cut."""
+    tree = inputs.complete_tree(4, 1.7)
+    rng = np.random.default_rng(4)
+    for L in range(1, 5):
+        cam = inputs.camera_along(inputs.random_direction(rng), fov=1.2, n=10, max_level=L, mode=3)
+        m, c = oracle.render(tree, cam, lib=lib)
+        assert (np.abs(m[c > 0] - L) <= 1e-13).all(), (L, m[c > 0].min(), m[c > 0].max())
+
+
 def pin_level_rule(lib):
     deep = inputs.Tree(np.array([1, 22], np.uint8), np.zeros((2, 3), np.int32),
                        np.array([[1] + [-1] * 7, [-1] * 8], np.int32), [np.ones((2, 8))])
@@ -278,7 +288,8 @@ def pin_quantisation(lib):
 
 
 ALL_PINS = [pin_golden, pin_quantisation, pin_uniform_axis, pin_uniform_oblique, pin_single_leaf,
-            pin_bruteforce, pin_mass, pin_split, pin_symmetry, pin_sortlast, pin_wmean_constant, pin_level_rule]
+            pin_bruteforce, pin_mass, pin_split, pin_symmetry, pin_sortlast, pin_wmean_constant, pin_level_rule,
+            pin_mean_level_uniform]
 
 
 def pin_slice(lib):

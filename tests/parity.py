@@ -2,7 +2,8 @@
 
 counts : bit-exact, every pixel.
 column : per-pixel |a - b| / b where b > 0, and a == 0 exactly where b == 0.
-wmean  : normwise |a - b| / max|b| (the line-of-sight velocity changes sign).
+wmean  : normwise |a - b| / max|b| (the line-of-sight velocity changes sign);
+         the mean-level mode likewise.
 max    : bit-exact (a maximum over the same float32 values), compared in the
          kernel's output precision.
 Tolerances: FP64 kernel 1e-12; FP32 compensated 1e-5.  The FP32 plain kernel is
@@ -23,7 +24,7 @@ def errors(mode, gpu_map, ref_map):
         zero_ok = bool((a[~pos] == 0).all())
         return {"max": float(rel.max(initial=0.0)), "p99": float(np.percentile(rel, 99)) if rel.size else 0.0,
                 "zero_ok": zero_ok}
-    if mode == 1:
+    if mode in (1, 3):
         scale = float(np.abs(b).max(initial=0.0))
         e = np.abs(a - b) / scale if scale > 0 else np.abs(a - b)
         return {"max": float(e.max(initial=0.0)), "p99": float(np.percentile(e, 99)) if e.size else 0.0,

@@ -374,3 +374,28 @@ def test_slice_map_matches_oracle(gpu):
             m64 = np.zeros((cam.ny, cam.nx), np.float64)
             amr.amr_slice(r.ctx, cam.with_(precision=amr.AMR_PREC_FP64), m64, None, 0)
             assert (m64 == ref).all(), k
+
+
+def test_mean_level_and_adaptive_blur(gpu):
+    """Sec. 2.2 adaptive blur: the mean-level map against the oracle, then the
+    blur of the GPU column map against the oracle blur of the same inputs."""
+    from oracle import blur as oblur
+    tree = tree_of("galaxy")
+    rng = np.random.default_rng(8)
+    # level 11 cells are a third of a pixel (left sharp), level-7 cells ~5 pixels (blurred)
+    cam = inputs.camera_along(inputs.random_direction(rng), centre=(0.5, 0.5, 0.5), fov=0.15, n=(96, 72),
+                              max_level=11, precision=amr.AMR_PREC_FP32_KAHAN)
+    lvl_cam = cam.with_(mode=amr.AMR_MODE_LEVEL)
+    ref_lv, rc = oracle.render(tree, lvl_cam)
+    with amr.Renderer(tree) as r:
+        col, _ = r.render(cam)
+        lv, c = r.render(lvl_cam)
+        assert_parity(3, 1, host(lv), host(c), ref_lv, rc, ctx="mean level")
+        out = torch.empty_like(col)
+        pixel = cam.fov[0] / cam.nx
+        amr.amr_blur(r.ctx, cam.nx, cam.ny, col, lv, pixel, out, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    ref = oblur.adaptive_blur(host(col).astype(np.float64), host(lv).astype(np.float64), pixel)
+    sig = oblur.sigma_map(host(lv), pixel)
+    assert (sig >= 0.5).any() and (sig < 0.5).any()     # the view mixes blurred and sharp pixels
+    assert np.abs(host(out) - ref).max() <= 1e-5 * np.abs(ref).max()

@@ -36,6 +36,7 @@ MUTANTS = {
     "exit_uses_lower_face_going_up": ("(i128)(k + 1) * size - X0[b]", "(i128)k * size - X0[b]"),
     "slice_point_on_face_goes_low": ("c |= (X0[b] >= mid) << b;", "c |= (X0[b] > mid) << b;"),
     "slice_ignores_cut": ("if (ch < 0 || lvl == vw.L) {", "if (ch < 0) {"),
+    "mean_level_off_by_one": ("nadd(&N, r * len * (double)lvl);", "nadd(&N, r * len * (double)(lvl + 1));"),
 }
 
 
