@@ -399,3 +399,43 @@ def test_mean_level_and_adaptive_blur(gpu):
     sig = oblur.sigma_map(host(lv), pixel)
     assert (sig >= 0.5).any() and (sig < 0.5).any()     # the view mixes blurred and sharp pixels
     assert np.abs(host(out) - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_server_timeout_cancel_budget_and_shutdown(gpu):
+    """Failure paths of the request server, all made on the host: a wait that
+    runs out of time, a queued request cancelled, a request over the memory
+    budget, and a context destroyed with work still queued."""
+    tree = tree_of("galaxy")
+    big = inputs.camera_along((0.3, 0.5, 0.8), fov=1.0, n=2048, max_level=tree.depth,
+                              precision=amr.AMR_PREC_FP32_KAHAN)
+    bufs = [(np.zeros((2048, 2048), np.float32), np.zeros((2048, 2048), np.int32)) for _ in range(4)]
+    with amr.Renderer(tree) as r:
+        amr.amr_server_config(r.ctx, slots=1, map_budget_bytes=40 << 20, max_batch=1)
+        tickets = [amr.amr_submit(r.ctx, big, m, c) for m, c in bufs]
+        with pytest.raises(amr.AmrError) as e:
+            amr.amr_wait(r.ctx, tickets[0], 0)           # the first render takes milliseconds
+        assert e.value.status == amr.AMR_E_TIMEOUT
+        amr.amr_cancel(r.ctx, tickets[3])                # still queued behind the others
+        with pytest.raises(amr.AmrError) as e:
+            amr.amr_wait(r.ctx, tickets[3], -1)
+        assert e.value.status == amr.AMR_E_CANCELLED
+        for t in tickets[:3]:
+            amr.amr_wait(r.ctx, t, 60_000_000)
+        with pytest.raises(amr.AmrError) as e:
+            amr.amr_cancel(r.ctx, tickets[0])            # finished and collected
+        assert e.value.status == amr.AMR_E_INVALID
+        ref, rc = r.render(big)
+        assert (bufs[0][0] == host(ref)).all() and (bufs[2][1] == host(rc)).all()
+        huge = big.with_(nx=8192, ny=8192)                # 512 MiB of map: over the 40 MiB budget
+        with pytest.raises(amr.AmrError) as e:
+            amr.amr_submit(r.ctx, huge, np.zeros(1, np.float32))
+        assert e.value.status == amr.AMR_E_OOM
+        st = r.stats()["server"]
+        assert st["done"] == 3 and st["queued"] == 0
+    # shutdown with requests still queued: they end cancelled, destroy returns
+    ctx = amr.amr_create(0)
+    amr.amr_load_octree(ctx, tree.n_oct, tree.level, tree.coord, tree.child, tree.fields, amr.AMR_F32)
+    amr.amr_server_config(ctx, slots=1, map_budget_bytes=40 << 20, max_batch=1)
+    for m, c in bufs:
+        amr.amr_submit(ctx, big, m, c)
+    amr.amr_destroy(ctx)
