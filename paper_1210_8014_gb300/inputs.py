@@ -413,3 +413,83 @@ def random_tree(rng: np.random.Generator, depth: int, p_refine: float = 0.4, n_f
     t = Tree(np.array(level, np.uint8), np.array(coord, np.int32), np.array(child, np.int32),
              [f.astype(dtype) for f in fields], {"kind": "random", "depth": depth})
     return t
+
+
+# --------------------------------------------------------------------------- tree files
+TREE_MAGIC = b"AMRTREE1"
+
+
+def save_tree(tree: Tree, path) -> None:
+    """Write a tree as one file: magic, a JSON header (sizes, dtypes, level
+    histogram, generator parameters, a CRC-32 of the payload) and the raw
+    little-endian arrays level, coord, child, fields in that order."""
+    import json
+    import zlib
+    arrays = [np.ascontiguousarray(tree.level, "<u1"), np.ascontiguousarray(tree.coord, "<i4"),
+              np.ascontiguousarray(tree.child, "<i4")]
+    fdt = "<f8" if tree.fields and tree.fields[0].dtype == np.float64 else "<f4"
+    arrays += [np.ascontiguousarray(f, fdt) for f in tree.fields]
+    crc = 0
+    for a in arrays:
+        crc = zlib.crc32(memoryview(a).cast("B"), crc)
+    lv = tree.level.astype(np.int64)
+    leaf_hist = np.bincount(np.repeat(lv, (tree.child < 0).sum(axis=1)), minlength=23)
+    header = {"n_oct": tree.n_oct, "n_fields": len(tree.fields), "field_dtype": fdt, "crc32": crc,
+              "leaf_hist": {str(l): int(n) for l, n in enumerate(leaf_hist) if n},
+              "info": {k: v for k, v in tree.info.items() if isinstance(v, (int, float, str, list, dict))}}
+    hb = json.dumps(header).encode()
+    with open(path, "wb") as f:
+        f.write(TREE_MAGIC)
+        f.write(len(hb).to_bytes(8, "little"))
+        f.write(hb)
+        for a in arrays:
+            f.write(memoryview(a).cast("B"))
+
+
+def load_tree(path) -> Tree:
+    """Read a file written by save_tree; raises ValueError on a bad magic,
+    truncation or a checksum mismatch."""
+    import json
+    import zlib
+    with open(path, "rb") as f:
+        if f.read(8) != TREE_MAGIC:
+            raise ValueError(f"{path}: not a tree file")
+        hlen = int.from_bytes(f.read(8), "little")
+        header = json.loads(f.read(hlen).decode())
+        n, nf, fdt = header["n_oct"], header["n_fields"], header["field_dtype"]
+        specs = [("<u1", (n,)), ("<i4", (n, 3)), ("<i4", (n, 8))] + [(fdt, (n, 8))] * nf
+        arrays, crc = [], 0
+        for dt, shape in specs:
+            count = int(np.prod(shape))
+            a = np.fromfile(f, dtype=dt, count=count)
+            if a.size != count:
+                raise ValueError(f"{path}: truncated")
+            crc = zlib.crc32(memoryview(a).cast("B"), crc)
+            arrays.append(a.reshape(shape))
+    if crc != header["crc32"]:
+        raise ValueError(f"{path}: checksum mismatch")
+    native = np.float64 if fdt == "<f8" else np.float32
+    return Tree(arrays[0].astype(np.uint8), arrays[1].astype(np.int32), arrays[2].astype(np.int32),
+                [a.astype(native) for a in arrays[3:]], dict(header.get("info", {})))
+
+
+def cached(name: str, make, cache_dir=None) -> Tree:
+    """make() once per name and keep the tree in cache_dir (env AMR_TREE_CACHE;
+    no caching when neither is set)."""
+    import os
+    from pathlib import Path
+    d = cache_dir or os.environ.get("AMR_TREE_CACHE")
+    if not d:
+        return make()
+    p = Path(d) / f"{name}.amrtree"
+    if p.exists():
+        try:
+            return load_tree(p)
+        except ValueError:
+            p.unlink()
+    t = make()
+    Path(d).mkdir(parents=True, exist_ok=True)
+    tmp = p.with_suffix(".tmp")
+    save_tree(t, tmp)
+    tmp.replace(p)
+    return t
