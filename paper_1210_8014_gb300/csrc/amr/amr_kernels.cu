@@ -204,7 +204,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   float Sf = 0.0f, cSf = 0.0f, Nf = 0.0f, cNf = 0.0f, Mf = 0.0f;
   int count = 0;
 
-  while (!bad) {
+  // Every step moves on at least one axis (the exit-face test always selects
+  // one), so the loop ends; the cap only guards against a corrupted tree.
+  while (count < kStepCap) {
     const size_t cell = (size_t)o * 8 + c;
     const F rho = load_field<F>(rho_base, cell);
 
@@ -308,6 +310,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
             if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
             k0 >>= lvl0 - lvl; k1 >>= lvl0 - lvl; k2 >>= lvl0 - lvl;
             coarser = true;
+            recompute();
           }
         }
         if (!coarser && ((r.y >> c) & 1u) && lvl < L) {
@@ -321,6 +324,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           if (o >= A.n_oct) { bad = true; break; }
           r = __ldg(&rec[o]);
           descend(lvl + 1, lvl, k0, k1, k2);
+          if (bad) break;
+          recompute();
         }
       } else {
         // Several axes at once, leaving the oct (an edge or corner): from the root.
@@ -337,6 +342,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
         dA = sel3(ea, aD[0], aD[1], aD[2]);
         descend(1, lvl, j0, j1, j2);
+        if (bad) break;
+        if (lvl != lvl0) recompute();
       }
     } else {
       // No links: neighbour by coordinates; leaving [0, 2^lvl) ends the ray.
@@ -360,6 +367,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           stack[lvl + 1] = o;
           r = __ldg(&rec[o]);
           descend(lvl + 1, lvl, j0, j1, j2);
+          if (bad) break;
+          recompute();
         }
       } else {
         // From the deepest ancestor both cells share (highest differing bit).
@@ -372,14 +381,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
         dA = sel3(ea, aD[0], aD[1], aD[2]);
         descend(q, lvl, j0, j1, j2);
+        if (bad) break;
+        if (lvl != lvl0) recompute();
       }
     }
-    if (lvl != lvl0) recompute();
-    if (count >= kStepCap) {
-      atomicExch(&A.q->error, (int)kDevStepCap);
-      break;
-    }
   }
+  if (count >= kStepCap) atomicExch(&A.q->error, (int)kDevStepCap);
   if (bad) {
     atomicExch(&A.q->error, (int)kDevBadOct);
     atomicExch(&A.q->err_oct, (int)o);
