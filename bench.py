@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--config", choices=("batch", "precision", "zoom", "serve"), default="batch")
+    ap.add_argument("--config", choices=("batch", "precision", "zoom", "serve", "tiny"), default="batch")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--graph", action="store_true", help="replay batches through CUDA graphs")
     ap.add_argument("--cams", type=int, default=64)
@@ -78,6 +78,10 @@ def workload(config, rank, n_cams, precision):
         name = (f"{n_cams}-camera batch, sizes 128^2..2048^2, fov 1..1/64, pixel-rule level cut, mixed modes; "
                 f"galaxy octree {tree.n_leaves} leaves (levels {min(map(int, tree.info['leaf_hist']))}-{tree.depth}, "
                 f"mass threshold 2^-22 of total)")
+    elif config == "tiny":
+        tree = inputs.plain_tree()
+        cams = [inputs.axis_camera(256, max_level=7, precision=precision)]
+        name = f"plain-method tiny tree ({tree.n_leaves} leaves, float64), +z view 256^2 at level 7, column"
     elif config == "precision":
         tree = inputs.cached("galaxy_precision", inputs.galaxy_precision_tree)
         cams = [c for c in inputs.galaxy_precision_cameras(tree, precisions=(precision,))]
