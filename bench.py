@@ -224,6 +224,48 @@ def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
                       f"({total_segs} segments, {total_t:.1f} s of oracle time)"}
 
 
+def aux_kernels(r, cams, stream, flush, reps=5):
+    """Time the slice map and the adaptive blur on one frame of the workload
+    (the 4th zoom frame): slice = one descent per pixel; blur = the
+    mean-level render it needs plus the two gather passes."""
+    import torch
+    from paper_1210_8014_gb300 import amr
+    cam = cams[min(3, len(cams) - 1)]
+    dev = r.torch.device(f"cuda:{r.device}")
+    m = torch.empty((cam.ny, cam.nx), dtype=torch.float32, device=dev)
+    lv = torch.empty_like(m)
+    lvl_i = torch.empty((cam.ny, cam.nx), dtype=torch.int32, device=dev)
+    out = torch.empty_like(m)
+
+    def timed(fn):
+        ts = []
+        for k in range(reps + 1):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    slice_ms = timed(lambda: amr.amr_slice(r.ctx, cam, m, lvl_i, 1, stream.cuda_stream))
+    level_cam = cam.with_(mode=amr.AMR_MODE_LEVEL)
+    level_ms = timed(lambda: amr.amr_render(r.ctx, level_cam, lv, None, 1, stream.cuda_stream))
+    amr.amr_render(r.ctx, cam, m, None, 1, stream.cuda_stream)
+    pixel = cam.fov[0] / cam.nx
+    blur_ms = timed(lambda: amr.amr_blur(r.ctx, cam.nx, cam.ny, m, lv, pixel, out, stream.cuda_stream))
+    torch.cuda.synchronize()
+    px = cam.nx * cam.ny
+    depth = float(lvl_i.float().mean())
+    return {"frame": f"{cam.nx}^2, fov {cam.fov[0]:g}, level {amr.amr_camera_check(r.ctx, cam)}",
+            "slice_ms": slice_ms, "slice_gpixels_per_s": px / (slice_ms * 1e-3) / 1e9,
+            "slice_mean_leaf_level": depth, "level_render_ms": level_ms, "blur_ms": blur_ms,
+            "blur_gpixels_per_s": px / (blur_ms * 1e-3) / 1e9}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -386,6 +428,7 @@ def run_ours(args):
     d2h = sum(m.nbytes + c.nbytes for m, c in zip(hmaps, hcnts))
     h2d = len(cams32) * 152
 
+    aux = aux_kernels(r, cams32, stream, flush) if args.config == "zoom" else None
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (ms32 * 1e-3) / 1e9
     algo_ops = sum(s_ * OPS_PER_SEG[c.mode] for s_, c in zip(seg_cam, cams32))
@@ -421,6 +464,7 @@ def run_ours(args):
         "timed_wall_s": wall32,
         "setup_s": {"generate": gen_s, "load": load_s},
         "regs": stats.get("regs"),
+        "aux_kernels": aux,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(tree, cams32)
