@@ -1,8 +1,8 @@
 /*
  * amr.h — C ABI of libamr: octree-AMR volume ray casting on one GB300 GPU.
  *
- * The operation is the ray-casting pass of Sec. 2.2 ("The volume ray casting
- * technique"): one ray per pixel; each leaf cell the ray crosses contributes its
+ * The operation is the ray-casting pass of Sec. 2.2 (the volume ray casting
+ * technique): one ray per pixel; each leaf cell the ray crosses contributes its
  * value times the length between the ray's entry and exit points on the cell
  * faces; contributions are added in any order.  The camera fixes the deepest
  * octree level read, so cells at that level act as leaves (Sec. 2, first
@@ -141,7 +141,7 @@ amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, voi
                             int32_t* const* counts, int out_on_device, void* cuda_stream);
 
 /*
- * Slice map (Sec. 3.3: the "Slicemap" tree search the authors moved to the
+ * Slice map (Sec. 3.3: the slice-map tree search the authors moved to the
  * GPU): for each pixel centre — the plane through cam->centre spanned by u, v,
  * the same pixel lattice and quantisation as the rays — the value of
  * cam->field_value in the leaf holding that point at the camera's level cut
@@ -154,8 +154,8 @@ amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t
                      void* cuda_stream);
 
 /*
- * Adaptive Gaussian blur (Sec. 2.2: the post-process that follows the local
- * image resolution, against the aliasing of coarse cells).  in, level, out:
+ * Adaptive Gaussian blur (Sec. 2.2: a post-process whose width follows how
+ * finely the mesh is resolved under each pixel, against coarse-cell aliasing).  in, level, out:
  * device float [ny][nx]; level is the AMR_MODE_LEVEL map of the same camera;
  * pixel is the pixel edge in box units (fov[0] / nx).  Per pixel, sigma =
  * 2^-level / (2 pixel) pixels (below 0.5: copied unchanged); separable, rows

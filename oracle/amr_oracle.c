@@ -38,7 +38,7 @@
  *   - wmean line-of-sight velocity = v . w (w as given, double).
  *
  * Procedure per ray, in the paper's order (Sec. 2.2): find where the ray enters
- * and leaves the box; starting at the entry, descend from the root "top-down"
+ * and leaves the box; starting at the entry, descend from the root
  * until a leaf (or a cell at the camera's level) contains the ray; compute the
  * exit point on that cell's faces; add value * length; continue from the exit
  * point with a fresh descent from the root, until the ray leaves the box.
@@ -222,7 +222,7 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
   int32_t cnt = 0;
   rtime t = tin;
   for (;;) {
-    /* Top-down descent from the root to the leaf holding the ray just after t. */
+    /* Descent from the root to the leaf holding the ray just after t. */
     int64_t oct = 0;
     int lvl = 1;
     int c;
@@ -352,7 +352,7 @@ int oracle_ray_origin(const oracle_camera* cam, int32_t i, int32_t j, int64_t* X
 }
 
 /*
- * Slice map (Sec. 3.3, "Slicemap", a tree search): for each pixel centre (on
+ * Slice map (Sec. 3.3, the slice-map tree search): for each pixel centre (on
  * the plane through the camera centre spanned by u and v), the value of the
  * leaf containing that point at the camera's level cut, and that leaf's level
  * (0 and 0 outside the box).  Containment is half-open: the point belongs to

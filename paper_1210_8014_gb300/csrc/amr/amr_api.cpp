@@ -720,7 +720,7 @@ amr_status linearise(int64_t n, const uint8_t* level, const int32_t* coord, cons
   return AMR_OK;
 }
 
-// Face-neighbour links (the "fully threaded tree" of RAMSES, Sec. 1), built in
+// Face-neighbour links (RAMSES keeps neighbour references per cell, Sec. 1), built in
 // breadth-first order from the parent's links.  For oct p and face f = 2 axis +
 // (side > 0): the oct of the same level across that face (>= 0), -1 outside
 // the box, or -(2 + 8 oct + cell) for the deepest existing cell covering the

@@ -1,6 +1,6 @@
 // Adaptive Gaussian blur (Sec. 2.2): a post-process whose filter size follows
-// the local image resolution, against the aliasing of coarse cells in images
-// that mix refinement levels.  The local resolution of a pixel is the
+// how finely the mesh is resolved under each pixel, against the aliasing of
+// coarse cells in images that mix refinement levels.  The local resolution of a pixel is the
 // density-weighted mean level of the leaves its ray crossed (an
 // AMR_MODE_LEVEL render of the same camera): cell edge h = 2^-level, Gaussian
 // sigma = h / (2 pixel) in pixels, no blur below half a pixel.  The filter is

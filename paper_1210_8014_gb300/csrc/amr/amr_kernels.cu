@@ -1,26 +1,28 @@
 // Octree-AMR ray casting kernels for sm_103a.
 //
-// One thread traces one pixel ray (Sec. 2.2: "for each pixel of the image, one
-// ray is shot").  Warps take 2-D pixel tiles from a device work queue shared by
-// every camera of a batch (Sec. 3.2: a master hands work to whichever worker is
-// free), so uneven cameras keep every SM busy until the last tile.
+// One thread traces one pixel's ray (Sec. 2.2 casts a single ray per pixel).
+// Warps take 2-D pixel tiles from a device work queue shared by every camera of
+// a batch (Sec. 3.2 hands work to whichever worker is free), so cameras of
+// uneven size keep every SM busy until the last tile.
 //
 // Per ray:
 //   set-up  : pixel centre in IEEE double (the only FP64 step of the FP32
 //             kernels), rounded to the 2^-36 lattice; box entry by exact
 //             comparisons of rational crossing times.
-//   descent : top-down from the root to the leaf holding the ray (Sec. 2.2),
+//   descent : from the root down to the leaf holding the ray (Sec. 2.2),
 //             choosing children by the exact side of the mid-planes at the
 //             entry time; stops at a leaf or at the camera's level (Sec. 2).
-//   step    : the exit face(s) of the current leaf are the earliest crossing
-//             times, compared by exact 64-bit cross-multiplication; the chord is
-//             the exact integer time difference times a per-camera factor;
-//             value x chord is accumulated; the next cell is reached by going
-//             up to the deepest oct shared with the neighbour (highest set bit
-//             of old xor new integer coordinates) and descending again.
+//   step    : three 32-bit terms give the exact order of the cell's exit
+//             times on the three axes; the chord is an exact integer time
+//             difference times per-camera factors; value x chord is added;
+//             the next cell is the same oct's neighbour (a bit flip of the
+//             cell index) or the oct named by a face link (a coarser leaf, or
+//             the end of the box); refined neighbours are descended into.
+//             Without links (the no-allocation entry point) the neighbour is
+//             reached through the stack of ancestor octs instead.
 //
 // Oct records are 8 bytes {index of the first child oct, 8-bit refinement
-// mask}; siblings are contiguous, so the child of cell c is
+// mask | level << 8}; siblings are contiguous, so the child of cell c is
 // first + popc(mask & ((1 << c) - 1)).  Field values are one array per field,
 // indexed oct * 8 + cell.
 #include "amr_internal.h"
@@ -31,8 +33,6 @@ namespace {
 
 constexpr long long kBox = 1LL << kFixBits;
 constexpr int kStepCap = 1 << 25;  // no ray at level <= 22 visits this many leaves
-
-__device__ __forceinline__ int cmp64(long long a, long long b) { return (a > b) - (a < b); }
 
 template <typename T>
 __device__ __forceinline__ T sel3(int i, T a, T b, T c) { return i == 0 ? a : (i == 1 ? b : c); }
@@ -118,7 +118,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   const float lf0 = cam.lamInvF[0], lf1 = cam.lamInvF[1], lf2 = cam.lamInvF[2];
   const float if0 = cam.invDF[0], if1 = cam.invDF[1], if2 = cam.invDF[2];
 
-  // ---- top-down descent (Sec. 2.2) -----------------------------------------
+  // ---- descent from the root (Sec. 2.2) ------------------------------------
   uint32_t stack[kMaxLevel + 2];
   uint32_t o = 0;
   uint2 r = __ldg(&rec[0]);

@@ -1,5 +1,5 @@
-// Slice map (Sec. 3.3: the "Slicemap" the authors ported to the GPU, a plain
-// tree search): for every pixel centre on the camera plane, the leaf holding
+// Slice map (Sec. 3.3: the slice-map tree search the authors ported to the
+// GPU): for every pixel centre on the camera plane, the leaf holding
 // that point at the camera's level cut.  One thread per pixel; the point is
 // quantised exactly as a ray origin, and the descent reads the cell index of
 // each level straight from the bits of the integer coordinates.

@@ -1,7 +1,7 @@
 """Sort-last domain decomposition of the ray-casting pass (Sec. 3.1, 3.2).
 
-The paper distributes the octree among processes ("sort last") and merges the
-partial images.  Because every leaf's contribution is added without ordering
+The paper distributes the octree among processes, each rendering its own part
+(sort-last compositing), and merges the partial images.  Because every leaf's contribution is added without ordering
 (Sec. 2.2), partial maps rendered over disjoint leaf domains combine exactly:
 
   column : sum of the partial column maps
