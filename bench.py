@@ -192,10 +192,19 @@ def max_over_ranks(x: float, device="cpu") -> float:
     return float(t.item())
 
 
-def replica_throughput(segments_per_rank: int, ms_max: float, world: int) -> float:
-    """Whole-job Gsegments/s: every rank renders its own batch of the same
-    shape (weak scaling), timed by the slowest rank."""
-    return world * segments_per_rank / (ms_max * 1e-3) / 1e9
+def sum_over_ranks(x: int, device="cpu") -> int:
+    """Sum of x over all ranks (every rank renders its own seeded batch)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def replica_throughput(total_segments: int, ms_max: float) -> float:
+    """Whole-job Gsegments/s: the segments every rank rendered in one step
+    (weak scaling: a fixed batch per rank), over the slowest rank's step time."""
+    return total_segments / (ms_max * 1e-3) / 1e9
 
 
 def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
@@ -406,9 +415,11 @@ def run_ours(args):
     t64, _ = timed(cams64, m64, c64, max(3, args.steps // 2))
     ms32 = float(np.mean(t32))
     ms64 = float(np.mean(t64))
+    total_segs = segs
     if world > 1:
         ms32 = max_over_ranks(ms32, dev)
-    value = replica_throughput(segs, ms32, world)
+        total_segs = sum_over_ranks(segs, dev)
+    value = replica_throughput(total_segs, ms32)
     value64 = segs / (ms64 * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: camera upload and map/count readback inside
@@ -440,7 +451,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
         "config": {"workload": name, "cameras": len(cams32), "rays_per_step": int(sum(c.nx * c.ny for c in cams32)),
-                   "segments_per_step": segs, "l2": "256 MiB buffer written between timed steps",
+                   "segments_per_step": total_segs, "segments_per_step_rank0": segs, "l2": "256 MiB buffer written between timed steps",
                    "options": tuned or amr.amr_get_options(r.ctx).as_dict(), "parallelism": f"replicas{world}"},
         "ms_per_frame": ms32 / len(cams32),
         "fp64_kernel": {"value": value64, "ms_per_step": ms64, "unit": UNIT,

@@ -81,7 +81,8 @@ def _rank_main(rank, world, port, out_dir):
             local = [oracle.render(dt, pc)[0] for pc in sortlast.partial_cameras(cam)]
             results.append(sortlast.merge_distributed(cam, local))
         mx = bench.max_over_ranks(10.0 + rank)
-        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), *results, mx=np.array([mx]))
+        sm = bench.sum_over_ranks(1000 + rank)
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), *results, mx=np.array([mx]), sm=np.array([sm]))
     finally:
         dist.destroy_process_group()
 
@@ -101,10 +102,11 @@ def test_sortlast_merge_across_gloo_ranks(tmp_path):
         tol = 0 if cam.mode == 2 else 1e-12 * np.abs(whole).max()
         assert np.abs(a - whole).max() <= tol
     assert float(r0["mx"][0]) == float(r1["mx"][0]) == 11.0
+    assert int(r0["sm"][0]) == int(r1["sm"][0]) == 2001
 
 
 def test_replica_throughput():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.replica_throughput(2 * 10 ** 9, 100.0, 1) == pytest.approx(20.0)
-    assert bench.replica_throughput(2 * 10 ** 9, 100.0, 4) == pytest.approx(80.0)
+    assert bench.replica_throughput(2 * 10 ** 9, 100.0) == pytest.approx(20.0)
+    assert bench.replica_throughput(8 * 10 ** 9, 100.0) == pytest.approx(80.0)
