@@ -439,3 +439,16 @@ def test_server_timeout_cancel_budget_and_shutdown(gpu):
     for m, c in bufs:
         amr.amr_submit(ctx, big, m, c)
     amr.amr_destroy(ctx)
+
+
+def test_large_batch_grows_launch_scratch(gpu):
+    """150 cameras in one batch (beyond the initial scratch of 64): every map
+    equals its camera rendered alone."""
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 150, seed=41, sizes=((32, 32), (17, 9), (40, 24)))
+    with amr.Renderer(tree) as r:
+        outs = r.render_batch(cams)
+        torch.cuda.synchronize()
+        for q in range(0, 150, 7):
+            m1, c1 = r.render(cams[q])
+            assert torch.equal(outs[q][0], m1) and torch.equal(outs[q][1], c1), q

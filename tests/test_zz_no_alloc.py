@@ -88,3 +88,28 @@ def test_noalloc_rejects_oversized_batch(setup):
                                      [None] * len(too_many))
     assert e.value.status == amr.AMR_E_INVALID
     assert "at most 256" in str(e.value)
+
+
+def test_noalloc_out_of_range_children_end_rays_cleanly(setup):
+    """The caller's records are not validated on the host; a first-child index
+    at or beyond n_oct ends the affected rays inside the kernel (its bounds
+    check runs before any read), and the call and the device stay healthy."""
+    tree, cams, expected, records, fields = setup
+    bad = records.clone()
+    refined = torch.nonzero((bad >> 32) != 0).flatten()
+    bad[refined[::3]] = (bad[refined[::3]] & ~0xFFFFFFFF) | (tree.n_oct + 5)
+    dev = torch.device("cuda:0")
+    maps = [torch.zeros((c.ny, c.nx), dtype=torch.float64 if c.precision == 0 else torch.float32, device=dev)
+            for c in cams]
+    cnts = [torch.zeros((c.ny, c.nx), dtype=torch.int32, device=dev) for c in cams]
+    amr.amr_render_batch_noalloc(tree.n_oct, bad, tree.depth, fields, amr.AMR_F32, cams, maps, cnts,
+                                 torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    total = sum(int(c.sum()) for c in cnts)
+    assert total < sum(int(e[1].sum()) for e in expected)
+    # the device is fine: an intact call right after reproduces the reference
+    amr.amr_render_batch_noalloc(tree.n_oct, records, tree.depth, fields, amr.AMR_F32, cams, maps, cnts,
+                                 torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for k, (cam, m, c) in enumerate(zip(cams, maps, cnts)):
+        assert (c.cpu().numpy() == expected[k][1]).all()
