@@ -291,16 +291,18 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         if (st2) k2 += s2;
         c ^= stepbits;
         bool coarser = false;
-        if (!inoct) {
-          // One axis leaves the oct: its face link is the same-level oct there,
-          // the coarser leaf covering that side, or -1 where the box ends.
-          const int v = __ldg(&A.nbr[(size_t)o * 6 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
+        // One axis leaves the oct: its face link is the same-level oct there,
+        // the coarser leaf covering that side, or -1 where the box ends.  The
+        // common case (a same-level oct) runs as predicated loads, no branch.
+        int v = (int)o;
+        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 6 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
+        if (v >= 0) {
+          if ((uint32_t)v >= A.n_oct) { bad = true; break; }
+          if (!inoct) r = __ldg(&rec[v]);
+          o = (uint32_t)v;
+        } else {
           if (v == -1) break;
-          if (v >= 0) {
-            o = (uint32_t)v;
-            if (o >= A.n_oct) { bad = true; break; }
-            r = __ldg(&rec[o]);
-          } else {
+          {
             const int cr = -v - 2;
             o = (uint32_t)cr >> 3;
             if (o >= A.n_oct) { bad = true; break; }
