@@ -91,7 +91,7 @@ typedef struct {
 /* Launch configuration; chosen by amr_autotune or set by hand. */
 typedef struct {
   int32_t tile_w, tile_h;     /* pixels per warp work item: tile_w*tile_h == 32 */
-  int32_t block_threads;      /* threads per block: 64..1024, multiple of 32 */
+  int32_t block_threads;      /* threads per block: 64..256, multiple of 32 (default 128) */
   int32_t blocks_per_sm;      /* persistent grid = SMs x this (0 = occupancy limit) */
   int32_t tiles_per_grab;     /* work items a warp takes from the queue at once (>= 1) */
   int32_t use_graph;          /* replay batches through a captured CUDA graph */

@@ -97,7 +97,7 @@ struct amr_ctx {
   int sms = 0;
   cudaStream_t stream = nullptr;
   DeviceTree tree;
-  amr_options opt{8, 4, 256, 0, 1, 0};
+  amr_options opt{8, 4, 128, 0, 1, 0};
   std::mutex launch_mu;  // guards slots and stats
   std::vector<LaunchSlot> slots;
   size_t next_slot = 0;
@@ -289,6 +289,8 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
     d.w[a] = c.w[a];
     d.wF[a] = (float)c.w[a];
   }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) d.facF[a][b] = a == b ? d.lamInvF[a] : d.lamInvF[a] * d.invDF[b];
   d.fov0 = c.fov[0];
   d.fov1 = c.fov[1];
   d.nxd = (double)c.nx;

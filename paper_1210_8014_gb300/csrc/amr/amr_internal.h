@@ -25,6 +25,9 @@ struct CamDev {
   double lamInv[3];         // lam / |D_a| (0 where D_a = 0)
   double invD[3];           // 1 / |D_a| (0 where D_a = 0)
   float lamInvF[3], invDF[3], wF[3];
+  // FP32 chord factor for entry axis a, exit axis b: lamInvF[a] * invDF[b]
+  // (rounded once) when b != a, lamInvF[a] when b == a; column 3 is padding.
+  float facF[3][4];
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;
   int32_t tiles_x;

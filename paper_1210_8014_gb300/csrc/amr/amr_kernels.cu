@@ -115,8 +115,6 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   const int s0 = D[0] > 0 ? 1 : -1, s1 = D[1] > 0 ? 1 : -1, s2 = D[2] > 0 ? 1 : -1;
   // Bit a set: the ray moves down axis a (its cells are entered from the high side).
   const int dirbits = (s0 < 0 ? 1 : 0) | (s1 < 0 ? 2 : 0) | (s2 < 0 ? 4 : 0);
-  const float lf0 = cam.lamInvF[0], lf1 = cam.lamInvF[1], lf2 = cam.lamInvF[2];
-  const float if0 = cam.invDF[0], if1 = cam.invDF[1], if2 = cam.invDF[2];
 
   // ---- descent from the root (Sec. 2.2) ------------------------------------
   uint32_t stack[kMaxLevel + 2];
@@ -255,9 +253,10 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         // K s is exact in float (|K| < 2^24, s a power of two); one rounding adds the remainder part.
         const float rest = up ? sel3(pair, p01, p02, p12) : sel3(pair, q01, q02, q12);
         const float numf = __fmaf_rn(__int2float_rn(K), sf, rest);
-        const float lb = sel3(b, lf0, lf1, lf2);
-        const float len = (b == ea) ? __fmul_rn(lb, sf)
-                                    : __fmul_rn(numf, __fmul_rn(sel3(ea, lf0, lf1, lf2), sel3(b, if0, if1, if2)));
+        // One per-camera factor per (entry, exit) axis pair, read from the
+        // camera record: no per-axis selects on the step.
+        const float fac = __ldg(&cam.facF[ea][b]);
+        const float len = __fmul_rn(b == ea ? sf : numf, fac);
         const float wgt = __fmul_rn((float)rho, len);
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
@@ -433,7 +432,9 @@ __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& ca
 // from the queue head; a tile index is mapped to its camera by binary search
 // over the per-camera tile prefix sums.
 template <int PREC, bool NB, typename F>
-__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchArgs A) {
+// 72 registers: 28 resident warps per SM with 128-thread blocks (80 registers
+// allow 24), at the cost of a few spilled words.
+__global__ void __maxnreg__(72) batch_kernel(const BatchArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long segs = 0;
   for (;;) {
