@@ -277,12 +277,13 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
     s2 += (double)q * (double)q;
   }
   d.lam = std::ldexp(std::sqrt(s2), -amr::kFixBits);
+  float lamInvF[3], invDF[3];
   for (int a = 0; a < 3; ++a) {
     const double ad = std::fabs((double)d.D[a]);
     d.invD[a] = ad > 0 ? 1.0 / ad : 0.0;
     d.lamInv[a] = ad > 0 ? d.lam / ad : 0.0;
-    d.invDF[a] = (float)d.invD[a];
-    d.lamInvF[a] = (float)d.lamInv[a];
+    invDF[a] = (float)d.invD[a];
+    lamInvF[a] = (float)d.lamInv[a];
     d.centre[a] = c.centre[a];
     d.u[a] = c.u[a];
     d.v[a] = c.v[a];
@@ -290,7 +291,12 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
     d.wF[a] = (float)c.w[a];
   }
   for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) d.facF[a][b] = a == b ? d.lamInvF[a] : d.lamInvF[a] * d.invDF[b];
+    for (int b = 0; b < 3; ++b) {
+      const float fac = a == b ? lamInvF[a] : lamInvF[a] * invDF[b];
+      std::memcpy(&d.chord[a][b].x, &fac, sizeof fac);
+      const int32_t adb = d.D[b] < 0 ? -d.D[b] : d.D[b];
+      d.chord[a][b].y = a < b ? adb - 1 : adb;
+    }
   d.fov0 = c.fov[0];
   d.fov1 = c.fov[1];
   d.nxd = (double)c.nx;

@@ -24,10 +24,11 @@ struct CamDev {
   double lam;               // box length per unit of ray parameter: |D|_2 2^-36
   double lamInv[3];         // lam / |D_a| (0 where D_a = 0)
   double invD[3];           // 1 / |D_a| (0 where D_a = 0)
-  float lamInvF[3], invDF[3], wF[3];
-  // FP32 chord factor for entry axis a, exit axis b: lamInvF[a] * invDF[b]
-  // (rounded once) when b != a, lamInvF[a] when b == a; column 3 is padding.
-  float facF[3][4];
+  float wF[3];
+  // Per (entry axis a, exit axis b): x = bits of the FP32 chord factor,
+  // float(lamInv[a]) * float(invD[b]) rounded once when b != a, float(lamInv[a])
+  // when b == a; y = the chord's K offset, |D_b| - 1 when a < b, else |D_b|.
+  int2 chord[3][3];
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;
   int32_t tiles_x;

@@ -171,7 +171,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   int F01, F02, F12;
   const int A0 = 2 * aD[0], A1 = 2 * aD[1], A2 = 2 * aD[2];
   long long r01 = 0, r02 = 0, r12 = 0;                  // remainders (FP64 chords)
-  float q01 = 0, q02 = 0, q12 = 0, p01 = 0, p02 = 0, p12 = 0;  // r and s - r as floats
+  // r and s - r of each pair as floats (FP32 chords), at 2 * pair + (ea < b);
+  // a small per-thread array read with one indexed load per step.
+  float restv[6];
   float sf = 0.0f;                                      // s as a float
   auto recompute = [&]() {
     const int sh = kFixBits - lvl;
@@ -189,8 +191,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     F02 = 2 * (int)E02 + (r02 != 0);
     F12 = 2 * (int)E12 + (r12 != 0);
     const long long s = 1LL << sh;
-    q01 = __ll2float_rn(r01); q02 = __ll2float_rn(r02); q12 = __ll2float_rn(r12);
-    p01 = __ll2float_rn(s - r01); p02 = __ll2float_rn(s - r02); p12 = __ll2float_rn(s - r12);
+    restv[0] = __ll2float_rn(r01); restv[1] = __ll2float_rn(s - r01);
+    restv[2] = __ll2float_rn(r02); restv[3] = __ll2float_rn(s - r02);
+    restv[4] = __ll2float_rn(r12); restv[5] = __ll2float_rn(s - r12);
     sf = __int_as_float((127 + sh) << 23);
   };
 
@@ -231,8 +234,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       const int pair = ea + b - 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
       const bool up = ea < b;
       const int E = sel3(pair, F01, F02, F12) >> 1;
-      const int aDb = sel3(b, aD[0], aD[1], aD[2]);
-      const int K = up ? aDb - E - 1 : aDb + E;
+      const int2 pc = __ldg(&cam.chord[ea][b]);  // {FP32 factor, K offset}
+      const int K = up ? pc.y - E : pc.y + E;
       const int e2 = kFixBits - lvl;  // s = 2^e2
       if (PREC == AMR_PREC_FP64) {
         const long long rp = sel3(pair, r01, r02, r12);
@@ -251,12 +254,10 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         }
       } else {
         // K s is exact in float (|K| < 2^24, s a power of two); one rounding adds the remainder part.
-        const float rest = up ? sel3(pair, p01, p02, p12) : sel3(pair, q01, q02, q12);
+        const float rest = restv[2 * pair + (up ? 1 : 0)];
         const float numf = __fmaf_rn(__int2float_rn(K), sf, rest);
-        // One per-camera factor per (entry, exit) axis pair, read from the
-        // camera record: no per-axis selects on the step.
-        const float fac = __ldg(&cam.facF[ea][b]);
-        const float len = __fmul_rn(b == ea ? sf : numf, fac);
+        // The factor comes with K from the camera record: no per-axis selects.
+        const float len = __fmul_rn(b == ea ? sf : numf, __int_as_float(pc.x));
         const float wgt = __fmul_rn((float)rho, len);
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
