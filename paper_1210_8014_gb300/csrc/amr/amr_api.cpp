@@ -11,6 +11,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -292,11 +293,23 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
   }
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
-      const float fac = a == b ? lamInvF[a] : lamInvF[a] * invDF[b];
+      const float fac = lamInvF[a] * invDF[b];
       std::memcpy(&d.chord[a][b].x, &fac, sizeof fac);
       const int32_t adb = d.D[b] < 0 ? -d.D[b] : d.D[b];
       d.chord[a][b].y = a < b ? adb - 1 : adb;
+      d.chord[a][b].z = a == b ? 0 : (a < b ? -1 : 1);
+      d.chord[a][b].w = a == b ? 6 : 2 * (a + b - 1) + (a < b ? 1 : 0);
     }
+  {
+    const int32_t A0 = 2 * std::abs(d.D[0]), A1 = 2 * std::abs(d.D[1]), A2 = 2 * std::abs(d.D[2]);
+    for (int sb = 0; sb < 8; ++sb) {
+      int32_t x = 0, y = 0, z = 0;
+      if (sb & 1) { x += A1; y += A2; }
+      if (sb & 2) { x -= A0; z += A2; }
+      if (sb & 4) { y -= A0; z -= A1; }
+      d.dF[sb] = make_int4(x, y, z, 0);
+    }
+  }
   d.fov0 = c.fov[0];
   d.fov1 = c.fov[1];
   d.nxd = (double)c.nx;

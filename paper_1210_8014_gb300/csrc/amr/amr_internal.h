@@ -25,10 +25,16 @@ struct CamDev {
   double lamInv[3];         // lam / |D_a| (0 where D_a = 0)
   double invD[3];           // 1 / |D_a| (0 where D_a = 0)
   float wF[3];
-  // Per (entry axis a, exit axis b): x = bits of the FP32 chord factor,
-  // float(lamInv[a]) * float(invD[b]) rounded once when b != a, float(lamInv[a])
-  // when b == a; y = the chord's K offset, |D_b| - 1 when a < b, else |D_b|.
-  int2 chord[3][3];
+  // Per (entry axis a, exit axis b), the chord's constants: x = bits of the
+  // FP32 factor float(lamInv[a]) * float(invD[b]) (rounded once); K = y + z E
+  // with (y, z) = (|D_b| - 1, -1) when a < b, (|D_b|, 1) when a > b and
+  // (|D_b|, 0) when a == b; w = index of the remainder part in the per-ray
+  // table {r01, s - r01, r02, s - r02, r12, s - r12, 0}: 2 pair + (a < b), or 6
+  // when a == b (the time is then s / |D_b| = |D_b| s / (|D_a| |D_b|)).
+  int4 chord[3][3];
+  // Increments of the exit-order terms (F01, F02, F12) for each set of stepped
+  // axes (bit a: axis a), 2|D| per crossed plane.
+  int4 dF[8];
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;
   int32_t tiles_x;

@@ -167,13 +167,14 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   // e = E s + r with 0 <= r < s, E a 32-bit integer, and r fixed while the
   // level holds (a step adds |D| s).  The loop keeps F = 2E + (r > 0): its
   // sign is the sign of e (F == 0 exactly when e == 0), a step adds 2|D|, and
-  // E = F >> 1.
+  // E = F >> 1.  The increments for each set of stepped axes come from the
+  // camera's table (one load instead of per-axis predicated adds).
   int F01, F02, F12;
-  const int A0 = 2 * aD[0], A1 = 2 * aD[1], A2 = 2 * aD[2];
   long long r01 = 0, r02 = 0, r12 = 0;                  // remainders (FP64 chords)
-  // r and s - r of each pair as floats (FP32 chords), at 2 * pair + (ea < b);
-  // a small per-thread array read with one indexed load per step.
-  float restv[6];
+  // r and s - r of each pair as floats (FP32 chords), at 2 * pair + (ea < b),
+  // and 0 at index 6; a small per-thread array read with one indexed load per step.
+  float restv[7];
+  restv[6] = 0.0f;
   float sf = 0.0f;                                      // s as a float
   auto recompute = [&]() {
     const int sh = kFixBits - lvl;
@@ -231,18 +232,19 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       //    K s + r,             K = |D_b| + E,  when ea > b  (e' = -e),
       // two non-negative parts (K >= 1, resp. K >= 0, since the chord is > 0).
       //   (t_exit - t_entry) = s / |D_b|                      (b == ea)
-      const int pair = ea + b - 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
-      const bool up = ea < b;
+      // The same axis twice (b == ea) gives s / |D_b|, written as K = |D_b|
+      // with no remainder part.  The camera's record for (ea, b) holds K's
+      // offset and sign, the factor and where the remainder part is: the step
+      // needs no per-axis selects.
+      const int4 pc = __ldg(&cam.chord[ea][b]);
+      const int pair = pc.w >> 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2 (3 when b == ea)
       const int E = sel3(pair, F01, F02, F12) >> 1;
-      const int2 pc = __ldg(&cam.chord[ea][b]);  // {FP32 factor, K offset}
-      const int K = up ? pc.y - E : pc.y + E;
-      const int e2 = kFixBits - lvl;  // s = 2^e2
+      const int K = pc.y + pc.z * E;
       if (PREC == AMR_PREC_FP64) {
+        const int e2 = kFixBits - lvl;  // s = 2^e2
         const long long rp = sel3(pair, r01, r02, r12);
-        const long long num = ((long long)K << e2) + (up ? (1LL << e2) - rp : rp);
-        const double lb = cam.lamInv[b];
-        const double len = (b == ea) ? lb * __longlong_as_double((long long)(1023 + e2) << 52)
-                                     : (double)num * (cam.lamInv[ea] * cam.invD[b]);
+        const long long rest = pc.w == 6 ? 0 : ((pc.w & 1) ? (1LL << e2) - rp : rp);
+        const double len = (double)(((long long)K << e2) + rest) * (cam.lamInv[ea] * cam.invD[b]);
         const double wgt = (double)rho * len;
         Sd += wgt;
         if (MODE == AMR_MODE_WMEAN) {
@@ -254,10 +256,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         }
       } else {
         // K s is exact in float (|K| < 2^24, s a power of two); one rounding adds the remainder part.
-        const float rest = restv[2 * pair + (up ? 1 : 0)];
-        const float numf = __fmaf_rn(__int2float_rn(K), sf, rest);
-        // The factor comes with K from the camera record: no per-axis selects.
-        const float len = __fmul_rn(b == ea ? sf : numf, __int_as_float(pc.x));
+        const float numf = __fmaf_rn(__int2float_rn(K), sf, restv[pc.w]);
+        const float len = __fmul_rn(numf, __int_as_float(pc.x));
         const float wgt = __fmul_rn((float)rho, len);
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
@@ -276,10 +276,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     ea = b;
 
     // Exit planes of the stepped axes move one cell on (valid while the level holds).
-    if (st0) { F01 += A1; F02 += A2; }
-    if (st1) { F01 -= A0; F12 += A2; }
-    if (st2) { F02 -= A0; F12 -= A1; }
     const int stepbits = (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
+    {
+      const int4 dF = __ldg(&cam.dF[stepbits]);
+      F01 += dF.x; F02 += dF.y; F12 += dF.z;
+    }
     const int lvl0 = lvl;
     if (NB) {
       // Neighbour at this level.  A step stays inside the oct when every
