@@ -112,8 +112,10 @@ amr_status amr_destroy(amr_ctx* ctx);
  * coord 0; child level = parent level + 1; child coord = 2 (parent coord + offset
  * of c); every non-root oct referenced exactly once; coordinates in range.
  * The arrays are renumbered breadth-first (siblings contiguous) into 8-byte oct
- * records {first child, refinement mask} plus one array per field, and copied to
- * device memory owned by the context; the caller may free its arrays on return.
+ * records {first child, refinement mask | level << 8}, 32-byte link blocks (six
+ * face links and the packed oct coordinates) and one array per field, and copied
+ * to device memory owned by the context (40 B + 8 x field size per oct); the
+ * caller may free its arrays on return.
  * Synchronous.
  */
 amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, const int32_t* coord,

@@ -48,7 +48,7 @@ amr_status fail(amr_status st, const char* fmt, ...) {
 
 struct DeviceTree {
   uint2* rec = nullptr;
-  int32_t* nbr = nullptr;  // [n_oct][6] face-neighbour links
+  int32_t* nbr = nullptr;  // [n_oct][8] link blocks: six face links + packed coordinates
   std::vector<void*> fields;
   int64_t n_oct = 0;
   int depth = 0;
@@ -895,6 +895,16 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
   std::vector<int32_t> nb;
   try {
     build_neighbours(rec, nb);
+    // One 32-byte block per oct: its six links, then its corner coordinates
+    // (even, < 2^22) halved and packed into 64 bits.
+    std::vector<int32_t> blocks((size_t)n_oct * 8);
+    for (int64_t p = 0; p < n_oct; ++p) {
+      for (int q = 0; q < 6; ++q) blocks[(size_t)p * 8 + q] = nb[(size_t)p * 6 + q];
+      const int32_t* cc = coord + (size_t)order[p] * 3;
+      const uint64_t pk = (uint64_t)(cc[0] >> 1) | ((uint64_t)(cc[1] >> 1) << 21) | ((uint64_t)(cc[2] >> 1) << 42);
+      std::memcpy(&blocks[(size_t)p * 8 + 6], &pk, sizeof pk);
+    }
+    nb.swap(blocks);
   } catch (const std::bad_alloc&) {
     return fail(AMR_E_OOM, "host memory for neighbour links");
   }
@@ -923,13 +933,13 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
       return fail(AMR_E_OOM, "device memory for field %d (%zu bytes)", f, fbytes);
     }
   }
-  if (cudaMalloc((void**)&t.nbr, (size_t)n_oct * 6 * sizeof(int32_t)) != cudaSuccess) {
+  if (cudaMalloc((void**)&t.nbr, (size_t)n_oct * 8 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     free_tree(t);
-    return fail(AMR_E_OOM, "device memory for %lld neighbour links", (long long)n_oct * 6);
+    return fail(AMR_E_OOM, "device memory for %lld neighbour link blocks", (long long)n_oct);
   }
   cudaError_t e = cudaMemcpy(t.rec, rec.data(), (size_t)n_oct * sizeof(uint2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(t.nbr, nb.data(), (size_t)n_oct * 6 * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.nbr, nb.data(), (size_t)n_oct * 8 * sizeof(int32_t), cudaMemcpyHostToDevice);
   std::vector<char> buf;
   try {
     buf.resize(fbytes);
@@ -949,7 +959,7 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
   t.n_oct = n_oct;
   t.depth = depth;
   t.f64 = field_dtype == AMR_F64;
-  t.bytes = (int64_t)(n_oct * (sizeof(uint2) + 6 * sizeof(int32_t)) + n_fields * fbytes);
+  t.bytes = (int64_t)(n_oct * (sizeof(uint2) + 8 * sizeof(int32_t)) + n_fields * fbytes);
   ctx->tree = std::move(t);
   return AMR_OK;
 }

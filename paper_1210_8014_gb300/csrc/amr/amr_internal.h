@@ -56,7 +56,9 @@ struct QueueBlock {
 
 struct BatchArgs {
   const uint2* rec;         // oct records {first child, refinement mask | level << 8}
-  const int32_t* nbr;       // [n_oct][6] face-neighbour links, or null (then the
+  const int32_t* nbr;       // [n_oct][8]: six face-neighbour links, then the oct's
+                            // corner coordinates halved, packed x | y << 21 | z << 42
+                            // in 64 bits; or null (then the
                             // kernel finds neighbours through its ancestor stack)
   uint32_t n_oct;
   int32_t n_cams;

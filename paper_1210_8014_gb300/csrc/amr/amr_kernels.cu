@@ -208,6 +208,15 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
 
   // Every step moves on at least one axis (the exit-face test always selects
   // one), so the loop ends; the cap only guards against a corrupted tree.
+  // With links the step keeps only (o, c); the cell's integer coordinates are
+  // rebuilt from the oct's packed corner (after its six links) where a level
+  // change or a corner needs them.
+  auto load_k = [&]() {
+    const unsigned long long pk = __ldg(reinterpret_cast<const unsigned long long*>(A.nbr + (size_t)o * 8 + 6));
+    k0 = (int)((pk & 0x1FFFFFull) << 1) | (c & 1);
+    k1 = (int)(((pk >> 21) & 0x1FFFFFull) << 1) | ((c >> 1) & 1);
+    k2 = (int)(((pk >> 42) & 0x1FFFFFull) << 1) | ((c >> 2) & 1);
+  };
   while (count < kStepCap) {
     const size_t cell = (size_t)o * 8 + c;
     const F rho = load_field<F>(rho_base, cell);
@@ -287,16 +296,13 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       // stepped axis moves from the oct's low cell up or from its high cell down.
       const bool inoct = ((c ^ dirbits) & stepbits) == 0;
       if (inoct || !(stepbits & (stepbits - 1))) {
-        if (st0) k0 += s0;
-        if (st1) k1 += s1;
-        if (st2) k2 += s2;
         c ^= stepbits;
         bool coarser = false;
         // One axis leaves the oct: its face link is the same-level oct there,
         // the coarser leaf covering that side, or -1 where the box ends.  The
         // common case (a same-level oct) runs as predicated loads, no branch.
         int v = (int)o;
-        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 6 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
+        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 8 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
         if (v >= 0) {
           if ((uint32_t)v >= A.n_oct) { bad = true; break; }
           if (!inoct) r = __ldg(&rec[v]);
@@ -311,13 +317,14 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
             r = __ldg(&rec[o]);
             lvl = (int)((r.y >> 8) & 31u);
             if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
-            k0 >>= lvl0 - lvl; k1 >>= lvl0 - lvl; k2 >>= lvl0 - lvl;
+            load_k();
             coarser = true;
             recompute();
           }
         }
         if (!coarser && ((r.y >> c) & 1u) && lvl < L) {
           // The neighbour is refined: enter its child oct, go on down by mid-planes.
+          load_k();
           const int sh = kFixBits - lvl;
           const int ka = sel3(ea, k0, k1, k2);
           const long long Xa = sel3(ea, X[0], X[1], X[2]);
@@ -332,6 +339,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         }
       } else {
         // Several axes at once, leaving the oct (an edge or corner): from the root.
+        load_k();
         const int j0 = k0 + (st0 ? s0 : 0);
         const int j1 = k1 + (st1 ? s1 : 0);
         const int j2 = k2 + (st2 ? s2 : 0);
