@@ -307,7 +307,15 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
       if (sb & 1) { x += A1; y += A2; }
       if (sb & 2) { x -= A0; z += A2; }
       if (sb & 4) { y -= A0; z -= A1; }
-      d.dF[sb] = make_int4(x, y, z, 0);
+      // w: the face-link slot of the lowest stepped axis b (2b when the ray
+      // moves down b, 2b + 1 when it moves up), | 8 when several axes step.
+      int w = 0;
+      if (sb) {
+        const int b = (sb & 1) ? 0 : ((sb & 2) ? 1 : 2);
+        w = 2 * b + (d.D[b] < 0 ? 0 : 1);
+        if (sb & (sb - 1)) w |= 8;
+      }
+      d.dF[sb] = make_int4(x, y, z, w);
     }
   }
   d.fov0 = c.fov[0];

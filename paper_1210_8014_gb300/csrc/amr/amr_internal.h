@@ -32,8 +32,9 @@ struct CamDev {
   // table {r01, s - r01, r02, s - r02, r12, s - r12, 0}: 2 pair + (a < b), or 6
   // when a == b (the time is then s / |D_b| = |D_b| s / (|D_a| |D_b|)).
   int4 chord[3][3];
-  // Increments of the exit-order terms (F01, F02, F12) for each set of stepped
-  // axes (bit a: axis a), 2|D| per crossed plane.
+  // For each set of stepped axes (bit a: axis a): x, y, z = increments of the
+  // exit-order terms F01, F02, F12 (2|D| per crossed plane); w = face-link slot
+  // of the lowest stepped axis, | 8 when more than one axis steps.
   int4 dF[8];
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;

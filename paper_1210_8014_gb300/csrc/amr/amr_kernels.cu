@@ -286,43 +286,39 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
 
     // Exit planes of the stepped axes move one cell on (valid while the level holds).
     const int stepbits = (st0 ? 1 : 0) | (st1 ? 2 : 0) | (st2 ? 4 : 0);
-    {
-      const int4 dF = __ldg(&cam.dF[stepbits]);
-      F01 += dF.x; F02 += dF.y; F12 += dF.z;
-    }
+    const int4 dF = __ldg(&cam.dF[stepbits]);
+    F01 += dF.x; F02 += dF.y; F12 += dF.z;
     const int lvl0 = lvl;
     if (NB) {
       // Neighbour at this level.  A step stays inside the oct when every
       // stepped axis moves from the oct's low cell up or from its high cell down.
       const bool inoct = ((c ^ dirbits) & stepbits) == 0;
-      if (inoct || !(stepbits & (stepbits - 1))) {
+      if (inoct || !(dF.w & 8)) {
         c ^= stepbits;
-        bool coarser = false;
-        // One axis leaves the oct: its face link is the same-level oct there,
-        // the coarser leaf covering that side, or -1 where the box ends.  The
-        // common case (a same-level oct) runs as predicated loads, no branch.
+        // One axis leaves the oct: its face link (the slot comes with the
+        // increments) is the same-level oct there, the coarser leaf covering
+        // that side, or -1 where the box ends.  The common case (a same-level
+        // oct) runs as predicated loads, no branch.
         int v = (int)o;
-        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 8 + 2 * b + ((dirbits >> b) & 1 ? 0 : 1)]);
+        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 8 + (dF.w & 7)]);
         if (v >= 0) {
           if ((uint32_t)v >= A.n_oct) { bad = true; break; }
           if (!inoct) r = __ldg(&rec[v]);
           o = (uint32_t)v;
         } else {
           if (v == -1) break;
-          {
-            const int cr = -v - 2;
-            o = (uint32_t)cr >> 3;
-            if (o >= A.n_oct) { bad = true; break; }
-            c = cr & 7;
-            r = __ldg(&rec[o]);
-            lvl = (int)((r.y >> 8) & 31u);
-            if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
-            load_k();
-            coarser = true;
-            recompute();
-          }
+          // A coarser leaf: an unrefined cell, so the test below skips it.
+          const int cr = -v - 2;
+          o = (uint32_t)cr >> 3;
+          if (o >= A.n_oct) { bad = true; break; }
+          c = cr & 7;
+          r = __ldg(&rec[o]);
+          lvl = (int)((r.y >> 8) & 31u);
+          if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
+          load_k();
+          recompute();
         }
-        if (!coarser && ((r.y >> c) & 1u) && lvl < L) {
+        if (((r.y >> c) & 1u) && lvl < L) {
           // The neighbour is refined: enter its child oct, go on down by mid-planes.
           load_k();
           const int sh = kFixBits - lvl;
