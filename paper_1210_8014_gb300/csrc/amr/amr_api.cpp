@@ -299,6 +299,9 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
       d.chord[a][b].y = a < b ? adb - 1 : adb;
       d.chord[a][b].z = a == b ? 0 : (a < b ? -1 : 1);
       d.chord[a][b].w = a == b ? 6 : 2 * (a + b - 1) + (a < b ? 1 : 0);
+      int sel[3] = {0, 0, 0};
+      if (a != b) sel[a + b - 1] = d.chord[a][b].z;
+      d.chordsel[a][b] = make_int4(sel[0], sel[1], sel[2], d.chord[a][b].z < 0 ? 1 : 0);
     }
   {
     const int32_t A0 = 2 * std::abs(d.D[0]), A1 = 2 * std::abs(d.D[1]), A2 = 2 * std::abs(d.D[2]);

@@ -32,6 +32,10 @@ struct CamDev {
   // table {r01, s - r01, r02, s - r02, r12, s - r12, 0}: 2 pair + (a < b), or 6
   // when a == b (the time is then s / |D_b| = |D_b| s / (|D_a| |D_b|)).
   int4 chord[3][3];
+  // z E by multiply-adds: (x, y, z) = z at the pair's slot of (F01, F02, F12),
+  // 0 elsewhere; w = 1 when z = -1.  Then z E = (x F01 + y F02 + z F12 + w) >> 1
+  // (F = 2E + [r > 0], so (1 - F) >> 1 = -E).
+  int4 chordsel[3][3];
   // For each set of stepped axes (bit a: axis a): x, y, z = increments of the
   // exit-order terms F01, F02, F12 (2|D| per crossed plane); w = face-link slot
   // of the lowest stepped axis, | 8 when more than one axis steps.

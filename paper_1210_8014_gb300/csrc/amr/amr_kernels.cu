@@ -245,13 +245,14 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       // with no remainder part.  The camera's record for (ea, b) holds K's
       // offset and sign, the factor and where the remainder part is: the step
       // needs no per-axis selects.
+      // z E is picked out of (F01, F02, F12) by multiply-adds (FMA pipe)
+      // instead of compares and selects (ALU pipe).
       const int4 pc = __ldg(&cam.chord[ea][b]);
-      const int pair = pc.w >> 1;  // {0,1} -> 0, {0,2} -> 1, {1,2} -> 2 (3 when b == ea)
-      const int E = sel3(pair, F01, F02, F12) >> 1;
-      const int K = pc.y + pc.z * E;
+      const int4 ps = __ldg(&cam.chordsel[ea][b]);
+      const int K = pc.y + ((F01 * ps.x + F02 * ps.y + F12 * ps.z + ps.w) >> 1);
       if (PREC == AMR_PREC_FP64) {
         const int e2 = kFixBits - lvl;  // s = 2^e2
-        const long long rp = sel3(pair, r01, r02, r12);
+        const long long rp = sel3(pc.w >> 1, r01, r02, r12);  // pair {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
         const long long rest = pc.w == 6 ? 0 : ((pc.w & 1) ? (1LL << e2) - rp : rp);
         const double len = (double)(((long long)K << e2) + rest) * (cam.lamInv[ea] * cam.invD[b]);
         const double wgt = (double)rho * len;
