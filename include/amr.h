@@ -210,7 +210,7 @@ amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket);
  * device-wide synchronisation, or a process held to a fixed memory footprint.
  * It needs no context: the caller passes the tree, the cameras and the outputs,
  * and the launch scratch (camera table, tile prefix sums, work-queue head) lives
- * in a fixed library-owned device array of under 192 KiB that every GPU loading
+ * in a fixed library-owned device array of under 224 KiB that every GPU loading
  * this library holds until exit.
  *   records   device, [n_oct] uint64: bits 0-31 index of the oct's first child
  *             oct, bits 32-39 its refinement mask (bit c set: cell c refined).

@@ -302,6 +302,7 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
       int sel[3] = {0, 0, 0};
       if (a != b) sel[a + b - 1] = d.chord[a][b].z;
       d.chordsel[a][b] = make_int4(sel[0], sel[1], sel[2], d.chord[a][b].z < 0 ? 1 : 0);
+      d.facD[a][b] = d.lamInv[a] * d.invD[b];
     }
   {
     const int32_t A0 = 2 * std::abs(d.D[0]), A1 = 2 * std::abs(d.D[1]), A2 = 2 * std::abs(d.D[2]);

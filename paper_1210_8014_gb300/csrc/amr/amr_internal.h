@@ -40,6 +40,8 @@ struct CamDev {
   // exit-order terms F01, F02, F12 (2|D| per crossed plane); w = face-link slot
   // of the lowest stepped axis, | 8 when more than one axis steps.
   int4 dF[8];
+  // FP64 chord factor for (entry a, exit b): lamInv[a] * invD[b].
+  double facD[3][3];
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;
   int32_t tiles_x;

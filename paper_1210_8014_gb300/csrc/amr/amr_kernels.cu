@@ -254,7 +254,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         const int e2 = kFixBits - lvl;  // s = 2^e2
         const long long rp = sel3(pc.w >> 1, r01, r02, r12);  // pair {0,1} -> 0, {0,2} -> 1, {1,2} -> 2
         const long long rest = pc.w == 6 ? 0 : ((pc.w & 1) ? (1LL << e2) - rp : rp);
-        const double len = (double)(((long long)K << e2) + rest) * (cam.lamInv[ea] * cam.invD[b]);
+        const double len = (double)(((long long)K << e2) + rest) * __ldg(&cam.facD[ea][b]);
         const double wgt = (double)rho * len;
         Sd += wgt;
         if (MODE == AMR_MODE_WMEAN) {
@@ -439,9 +439,10 @@ __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& ca
 // from the queue head; a tile index is mapped to its camera by binary search
 // over the per-camera tile prefix sums.
 template <int PREC, bool NB, typename F>
-// 72 registers: 28 resident warps per SM with 128-thread blocks (80 registers
-// allow 24), at the cost of a few spilled words.
-__global__ void __maxnreg__(72) batch_kernel(const BatchArgs A) {
+// 56 registers: 36 resident warps per SM with 128-thread blocks (72 registers
+// allow 28, 80 allow 24).  The step loop is latency-bound per warp, so the
+// extra warps pay for the spilled words (measured: 56 beats 64, 72 and 48).
+__global__ void __maxnreg__(56) batch_kernel(const BatchArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long segs = 0;
   for (;;) {

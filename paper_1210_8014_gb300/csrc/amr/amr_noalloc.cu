@@ -30,7 +30,7 @@ constexpr size_t kTileInts = (size_t)amr::kMaxPrecisions * (kMaxCams + 1);
 constexpr size_t kTilesOff = up(kCamBytes);
 constexpr size_t kQueueOff = kTilesOff + up(kTileInts * sizeof(int32_t));
 constexpr size_t kScratchBytes = kQueueOff + up(amr::kMaxPrecisions * sizeof(amr::QueueBlock));
-static_assert(kScratchBytes <= 192 * 1024, "no-allocation scratch must stay modest");
+static_assert(kScratchBytes <= 224 * 1024, "no-allocation scratch must stay modest");
 
 constexpr int kMaxDevices = 64;
 
