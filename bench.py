@@ -422,9 +422,9 @@ def run_ours(args):
     value = replica_throughput(total_segs, ms32)
     value64 = segs / (ms64 * 1e-3) / 1e9
 
-    # end to end through the C ABI with host buffers: camera upload and map/count readback inside
-    # Page-locked host buffers (what a serving client would keep): the
-    # readback runs at the host link's DMA rate.
+    # end to end through the C ABI with host buffers: camera upload and map/count readback inside.
+    # Page-locked host buffers (what a serving client would keep): the kernel
+    # writes the maps and counts straight into them over the host link.
     hmaps = [torch.empty((c.ny, c.nx), dtype=torch.float32, pin_memory=True).numpy() for c in cams32]
     hcnts = [torch.empty((c.ny, c.nx), dtype=torch.int32, pin_memory=True).numpy() for c in cams32]
     amr.amr_render_batch(r.ctx, cams32, hmaps, hcnts, 0)

@@ -128,7 +128,10 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
  * counts.  out_on_device != 0: both are device pointers and the call returns once
  * the work is enqueued on `cuda_stream` (a cudaStream_t; NULL = the CUDA default
  * stream); out_on_device == 0: host pointers, and the call returns when the
- * results are in them.
+ * results are in them.  Page-locked host buffers that are mapped into the
+ * device's address space (cudaHostAlloc, or cudaHostRegister with mapping) are
+ * written by the kernel itself over the host link, with no copy afterwards;
+ * pageable buffers go through device staging and a copy.
  */
 amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* count_out,
                       int out_on_device, void* cuda_stream);

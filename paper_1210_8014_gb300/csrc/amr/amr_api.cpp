@@ -534,6 +534,20 @@ amr_status ensure_stage(amr_ctx* ctx, int64_t bytes) {
   return AMR_OK;
 }
 
+// Device address of a host buffer the GPU can write directly: page-locked
+// memory mapped into the device's address space (cudaHostAlloc, or
+// cudaHostRegister with mapping).  On a GB300 these writes travel over the
+// NVLink-C2C host link while the kernel runs, so no copy follows.  Null for
+// pageable memory.
+void* host_alias(void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps, int32_t* const* counts,
                        int out_on_device, void* cuda_stream) {
   if (!ctx) return fail(AMR_E_INVALID, "null context");
@@ -543,17 +557,11 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
   const amr_options opt = ctx->opt;
   std::vector<CamDev> dev(n);
   std::vector<int> precs(n);
-  int64_t stage_bytes = 0;
-  std::vector<int64_t> off(n);
   for (int i = 0; i < n; ++i) {
     amr_status st = canonicalise(ctx, cams[i], opt.tile_w, opt.tile_h, dev[i]);
     if (st != AMR_OK) return fail(st, "camera %d: %s", i, g_err.c_str());
     if (!maps[i]) return fail(AMR_E_INVALID, "camera %d: null map pointer", i);
     precs[i] = cams[i].precision;
-    off[i] = stage_bytes;
-    const int64_t px = (int64_t)cams[i].nx * cams[i].ny;
-    stage_bytes += ((map_bytes(cams[i]) + 255) / 256) * 256;
-    if (counts && counts[i]) stage_bytes += ((px * 4 + 255) / 256) * 256;
   }
   cudaStream_t stream = (cudaStream_t)cuda_stream;  // NULL: the CUDA default stream
   if (out_on_device) {
@@ -564,17 +572,40 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
     LaunchSlot* s = nullptr;
     return enqueue(ctx, opt, dev, precs, stream, &s);
   }
-  amr_status st = ensure_stage(ctx, stage_bytes);
-  if (st != AMR_OK) return st;
+  // Host outputs: a camera whose map (and counts) the GPU can address is
+  // written in place; the others go to device staging and are copied back.
+  std::vector<char> staged(n, 0);
+  std::vector<int64_t> off(n, 0);
+  int64_t stage_bytes = 0;
   for (int i = 0; i < n; ++i) {
+    void* m = host_alias(maps[i]);
+    void* c = (counts && counts[i]) ? host_alias(counts[i]) : nullptr;
+    if (m && (c || !(counts && counts[i]))) {
+      dev[i].map = m;
+      dev[i].counts = (int32_t*)c;
+      continue;
+    }
+    staged[i] = 1;
+    off[i] = stage_bytes;
+    const int64_t px = (int64_t)cams[i].nx * cams[i].ny;
+    stage_bytes += ((map_bytes(cams[i]) + 255) / 256) * 256;
+    if (counts && counts[i]) stage_bytes += ((px * 4 + 255) / 256) * 256;
+  }
+  if (stage_bytes) {
+    amr_status st = ensure_stage(ctx, stage_bytes);
+    if (st != AMR_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!staged[i]) continue;
     char* base = (char*)ctx->stage + off[i];
     dev[i].map = base;
     dev[i].counts = (counts && counts[i]) ? (int32_t*)(base + ((map_bytes(cams[i]) + 255) / 256) * 256) : nullptr;
   }
   LaunchSlot* s = nullptr;
-  st = enqueue(ctx, opt, dev, precs, stream, &s);
+  amr_status st = enqueue(ctx, opt, dev, precs, stream, &s);
   if (st != AMR_OK) return st;
   for (int i = 0; i < n; ++i) {
+    if (!staged[i]) continue;
     CUDA_TRY(cudaMemcpyAsync(maps[i], dev[i].map, (size_t)map_bytes(cams[i]), cudaMemcpyDeviceToHost, stream));
     if (dev[i].counts)
       CUDA_TRY(cudaMemcpyAsync(counts[i], dev[i].counts, (size_t)cams[i].nx * cams[i].ny * 4, cudaMemcpyDeviceToHost,

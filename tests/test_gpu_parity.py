@@ -183,6 +183,37 @@ def test_host_output_path(gpu):
         assert (mb[0] == host(md)).all() and (mb[1] == host(m2)).all()
 
 
+def test_host_output_page_locked_written_in_place(gpu):
+    """Page-locked host maps are written by the kernel directly (no staging);
+    a batch that mixes them with pageable buffers gives the same results as
+    device outputs, for every camera, and stale values never survive."""
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 6, seed=23)
+    with amr.Renderer(tree) as r:
+        ref = [(host(m), host(c)) for m, c in r.render_batch(cams)]
+        torch.cuda.synchronize()
+        pinned = [k % 2 == 0 for k in range(len(cams))]
+        maps, cnts = [], []
+        for k, c in enumerate(cams):
+            dt = torch.float64 if c.precision == 0 else torch.float32
+            if pinned[k]:
+                maps.append(torch.full((c.ny, c.nx), float("nan"), dtype=dt, pin_memory=True).numpy())
+                cnts.append(torch.full((c.ny, c.nx), -7, dtype=torch.int32, pin_memory=True).numpy())
+            else:
+                maps.append(np.full((c.ny, c.nx), np.nan, np.float64 if c.precision == 0 else np.float32))
+                cnts.append(np.full((c.ny, c.nx), -7, np.int32))
+        amr.amr_render_batch(r.ctx, cams, maps, cnts, 0)
+        for k in range(len(cams)):
+            assert np.array_equal(cnts[k], ref[k][1]), k
+            assert np.array_equal(maps[k], ref[k][0]), k
+        # maps only (counts NULL), all page-locked
+        maps2 = [torch.zeros((c.ny, c.nx), dtype=torch.float64 if c.precision == 0 else torch.float32,
+                             pin_memory=True).numpy() for c in cams]
+        amr.amr_render_batch(r.ctx, cams, maps2, None, 0)
+        for k in range(len(cams)):
+            assert np.array_equal(maps2[k], ref[k][0]), k
+
+
 def test_deterministic(gpu):
     tree = tree_of("galaxy")
     cams = mixed_batch(tree, 6, seed=11)
