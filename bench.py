@@ -505,7 +505,10 @@ def run_serve(args):
         for mode in (0, 1, 2):
             c = reqs[0][1].with_(nx=n, ny=n, mode=mode)
             amr.amr_render(r.ctx, c, np.empty((n, n), np.float32), np.empty((n, n), np.int32), 0)
-    bufs = {n: [(np.empty((n, n), np.float32), np.empty((n, n), np.int32)) for _ in range(48)]
+    # page-locked result buffers, as a serving client keeps them: the kernel
+    # writes each request's map and counts into them in place
+    bufs = {n: [(torch.empty((n, n), dtype=torch.float32, pin_memory=True).numpy(),
+                 torch.empty((n, n), dtype=torch.int32, pin_memory=True).numpy()) for _ in range(48)]
             for n in inputs.SIZES_SERVE}
     tickets, done_segments = [], [0]
     import queue as _q

@@ -193,9 +193,10 @@ amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t
  * returns at once with a ticket; a server thread admits queued requests while
  * free slots and the map-memory budget allow, renders the admitted set as one
  * batch on one of several streams (so a batch admitted while others run overlaps
- * them on the device), and copies each result into the caller's HOST buffers
+ * them on the device), and delivers each result into the caller's HOST buffers
  * `map` / `counts` (nullable), which must stay valid until amr_wait returns for
- * the ticket.  amr_wait blocks until the ticket completes or timeout_us elapses
+ * the ticket: page-locked buffers mapped into the device's address space are
+ * written by the kernel in place, others through a slot buffer and a copy.  amr_wait blocks until the ticket completes or timeout_us elapses
  * (AMR_E_TIMEOUT; the request stays queued; timeout_us < 0 waits forever).
  * amr_server_config sets the slot count (concurrent batches, 1..8) and the map
  * memory budget in bytes (0 = 1 GiB); call it before the first amr_submit.

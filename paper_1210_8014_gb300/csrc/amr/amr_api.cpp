@@ -663,10 +663,20 @@ void server_worker(amr_ctx* ctx, ServerSlot* slot) {
       ctx->srv_inflight++;
       ctx->srv_max_inflight = std::max(ctx->srv_max_inflight, ctx->srv_inflight);
     }
-    // Device outputs in this slot's buffer, then copies into the callers' buffers.
+    // Callers' page-locked buffers the GPU can address are written in place;
+    // the other requests render into this slot's buffer and are copied back.
     int64_t need = 0;
     std::vector<int64_t> off(batch.size());
+    std::vector<void*> hmap(batch.size(), nullptr);
+    std::vector<int32_t*> hcnt(batch.size(), nullptr);
     for (size_t i = 0; i < batch.size(); ++i) {
+      void* m = host_alias(batch[i]->map);
+      void* c = batch[i]->counts ? host_alias(batch[i]->counts) : nullptr;
+      if (m && (c || !batch[i]->counts)) {
+        hmap[i] = m;
+        hcnt[i] = (int32_t*)c;
+        continue;
+      }
       off[i] = need;
       need += ((batch[i]->bytes + 255) / 256) * 256;
     }
@@ -690,6 +700,11 @@ void server_worker(amr_ctx* ctx, ServerSlot* slot) {
       std::vector<int32_t*> cnts(batch.size());
       for (size_t i = 0; i < batch.size(); ++i) {
         cams[i] = batch[i]->cam;
+        if (hmap[i]) {
+          maps[i] = hmap[i];
+          cnts[i] = hcnt[i];
+          continue;
+        }
         maps[i] = (char*)slot->dbuf + off[i];
         const int64_t mb = map_bytes(cams[i]);
         cnts[i] = batch[i]->counts ? (int32_t*)((char*)maps[i] + ((mb + 255) / 256) * 256) : nullptr;
@@ -697,6 +712,7 @@ void server_worker(amr_ctx* ctx, ServerSlot* slot) {
       st = render_impl(ctx, (int32_t)batch.size(), cams.data(), maps.data(), cnts.data(), 1, slot->stream);
       if (st == AMR_OK) {
         for (size_t i = 0; i < batch.size() && st == AMR_OK; ++i) {
+          if (hmap[i]) continue;
           if (cudaMemcpyAsync(batch[i]->map, maps[i], (size_t)map_bytes(cams[i]), cudaMemcpyDeviceToHost,
                               slot->stream) != cudaSuccess)
             st = AMR_E_CUDA;

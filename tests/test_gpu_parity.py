@@ -306,15 +306,22 @@ def test_autotune_keeps_results(gpu):
 
 def test_server_alone_vs_mix(gpu):
     """Requests submitted together overlap on the device; each result equals
-    the same camera rendered alone."""
+    the same camera rendered alone.  Every other request brings page-locked
+    buffers (written in place by the kernel), the rest pageable ones (slot
+    buffer and copy), so batches mix both deliveries."""
     tree = tree_of("galaxy")
     cams = mixed_batch(tree, 24, seed=9)
     with amr.Renderer(tree) as r:
         amr.amr_server_config(r.ctx, slots=3, map_budget_bytes=8 << 20, max_batch=6)
         bufs, tickets = [], []
-        for cam in cams:
-            mh = np.zeros((cam.ny, cam.nx), np.float64 if cam.precision == 0 else np.float32)
-            ch = np.zeros((cam.ny, cam.nx), np.int32)
+        for k, cam in enumerate(cams):
+            if k % 2:
+                dt = torch.float64 if cam.precision == 0 else torch.float32
+                mh = torch.zeros((cam.ny, cam.nx), dtype=dt, pin_memory=True).numpy()
+                ch = torch.zeros((cam.ny, cam.nx), dtype=torch.int32, pin_memory=True).numpy()
+            else:
+                mh = np.zeros((cam.ny, cam.nx), np.float64 if cam.precision == 0 else np.float32)
+                ch = np.zeros((cam.ny, cam.nx), np.int32)
             bufs.append((mh, ch))
             tickets.append(amr.amr_submit(r.ctx, cam, mh, ch))
         for t in tickets:
