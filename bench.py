@@ -164,23 +164,43 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(config):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source."""
+def recorded_profile(config):
+    """Figures of the committed ncu summary for this workload (DRAM bytes per
+    launch, cache hit rates), if it was taken on the current kernel source."""
     f = ROOT / "profiles" / f"batch_kernel_{config}_traffic.txt"
     if not f.exists():
-        return None
+        return {}
     kv = {}
     for line in f.read_text().splitlines():
-        if ":" in line:
+        if ":" in line and not line.lstrip().startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_sha") != kernel_source_hash():
+        return {}
+    out = {}
+    for key in ("dram_bytes_per_launch_full_workload", "l1_sector_hit_pct", "l2_sector_hit_pct"):
+        try:
+            out[key] = float(kv[key])
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
+def recorded_traffic(config):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    return recorded_profile(config).get("dram_bytes_per_launch_full_workload")
+
+
+def dram_view(prof, ms, peak):
+    """Measured DRAM traffic (ncu, per launch) as GB/s over the live kernel
+    time, its fraction of the measured copy bandwidth, and the cache hit
+    rates of the same summary; None without a summary for this kernel source."""
+    if "dram_bytes_per_launch_full_workload" not in prof:
         return None
-    try:
-        return float(kv["dram_bytes_per_launch_full_workload"])
-    except (KeyError, ValueError):
-        return None
+    gbs = prof["dram_bytes_per_launch_full_workload"] / (ms * 1e-3) / 1e9
+    return {"gbs": gbs, "frac": gbs / peak, "l1_sector_hit_pct": prof.get("l1_sector_hit_pct"),
+            "l2_sector_hit_pct": prof.get("l2_sector_hit_pct")}
 
 
 def max_over_ranks(x: float, device="cpu") -> float:
@@ -207,13 +227,10 @@ def replica_throughput(total_segments: int, ms_max: float) -> float:
     return total_segments / (ms_max * 1e-3) / 1e9
 
 
-def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
-    """The oracle as it stands, on a bounded random sample of the batch's rays."""
-    import oracle
+def _oracle_sample(oracle, lib, tree, cams, budget_s, threads, seed):
+    """Segments/s of the oracle on random rays of the cameras, growing the
+    sample until it has taken about budget_s of oracle time."""
     rng = np.random.default_rng(seed)
-    threads = os.cpu_count() or 1
-    lib = oracle.load()
-    tree = oracle.prepare(tree)
     per_cam = 8
     total_segs, total_t, total_rays = 0, 0.0, 0
     while True:
@@ -228,9 +245,21 @@ def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
         if total_t >= budget_s or per_cam >= 65536:
             break
         per_cam = int(min(65536, per_cam * max(2.0, budget_s / max(total_t, 1e-3) * 0.6)))
-    return {"value": total_segs / total_t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{total_rays} random rays spread over the {len(cams)} cameras "
-                      f"({total_segs} segments, {total_t:.1f} s of oracle time)"}
+    return total_segs / total_t / 1e9, (f"{total_rays} random rays spread over the {len(cams)} cameras "
+                                        f"({total_segs} segments, {total_t:.1f} s of oracle time)")
+
+
+def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
+    """The oracle as it stands, on a bounded random sample of the batch's rays:
+    on all host cores (the reported value) and on one thread beside it."""
+    import oracle
+    threads = os.cpu_count() or 1
+    lib = oracle.load()
+    tree = oracle.prepare(tree)
+    value, sample = _oracle_sample(oracle, lib, tree, cams, budget_s, threads, seed)
+    v1, s1 = _oracle_sample(oracle, lib, tree, cams, min(3.0, budget_s), 1, seed + 1)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": s1}}
 
 
 def aux_kernels(r, cams, stream, flush, reps=5):
@@ -467,7 +496,8 @@ def run_ours(args):
                      "algorithmic_ops_per_launch": algo_ops,
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                             "bytes_per_segment": BYTES_PER_SEG}},
+                             "bytes_per_segment": BYTES_PER_SEG,
+                             "dram": dram_view(recorded_profile(args.config), ms32, peak)}},
         "e2e": {"value": segs / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,
