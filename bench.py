@@ -458,6 +458,7 @@ def run_ours(args):
     hcnts = [torch.empty((c.ny, c.nx), dtype=torch.int32, pin_memory=True).numpy() for c in cams32]
     amr.amr_render_batch(r.ctx, cams32, hmaps, hcnts, 0)
     e2e_t = []
+    h2d_before = r.stats()["h2d_bytes"]
     for _ in range(max(3, args.steps // 2)):
         flush.fill_(1)
         torch.cuda.synchronize()
@@ -466,7 +467,9 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - a)
     e2e_ms = float(np.mean(e2e_t)) * 1e3
     d2h = sum(m.nbytes + c.nbytes for m, c in zip(hmaps, hcnts))
-    h2d = len(cams32) * 152
+    # what the library uploaded per step (camera records, tile prefix sums,
+    # pixel-offset tables), counted by the library itself
+    h2d = (r.stats()["h2d_bytes"] - h2d_before) // len(e2e_t)
 
     aux = aux_kernels(r, cams32, stream, flush) if args.config == "zoom" else None
     peak, peak_kind = measured_peaks()

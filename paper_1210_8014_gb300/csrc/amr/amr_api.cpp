@@ -71,6 +71,9 @@ struct LaunchSlot {
   int n_groups = 0;
   cudaGraphExec_t gexec = nullptr;  // captured launch sequence of this slot
   std::vector<int64_t> gkey;        // batch shape it was captured for
+  double* h_st = nullptr;           // pixel-centre offset tables, pinned mirror
+  double* d_st = nullptr;
+  int64_t st_cap = 0;               // doubles
 };
 
 struct Request {
@@ -108,6 +111,7 @@ struct amr_ctx {
   int64_t stage_cap = 0;
   // stats
   int64_t n_renders = 0, n_cams = 0, n_rays = 0;
+  int64_t n_h2d_bytes = 0;  // camera tables, tile prefix sums and offset tables uploaded
   unsigned long long n_segments = 0;
   int64_t n_dev_errors = 0;
   double last_batch_ms = 0.0;
@@ -146,6 +150,8 @@ void free_slot(LaunchSlot& s) {
   if (s.d_cams) cudaFree(s.d_cams);
   if (s.d_tiles) cudaFree(s.d_tiles);
   if (s.d_q) cudaFree(s.d_q);
+  if (s.h_st) cudaFreeHost(s.h_st);
+  if (s.d_st) cudaFree(s.d_st);
   s = LaunchSlot{};
 }
 
@@ -170,6 +176,53 @@ amr_status grow_slot(LaunchSlot& s, int n) {
     return fail(AMR_E_OOM, "cannot allocate launch scratch for %d cameras", n);
   }
   s.cap = cap;
+  return AMR_OK;
+}
+
+// Room for n doubles of pixel-centre offset tables in a slot.
+amr_status grow_st(LaunchSlot& s, int64_t n) {
+  if (s.st_cap >= n && s.h_st) return AMR_OK;
+  if (s.gexec) cudaGraphExecDestroy(s.gexec);
+  s.gexec = nullptr;
+  s.gkey.clear();
+  const int64_t cap = std::max<int64_t>(n, std::max<int64_t>(1 << 16, s.st_cap * 2));
+  if (s.h_st) cudaFreeHost(s.h_st);
+  if (s.d_st) cudaFree(s.d_st);
+  s.h_st = nullptr;
+  s.d_st = nullptr;
+  s.st_cap = 0;
+  if (cudaMallocHost((void**)&s.h_st, (size_t)cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&s.d_st, (size_t)cap * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AMR_E_OOM, "cannot allocate %lld pixel offsets", (long long)n);
+  }
+  s.st_cap = cap;
+  return AMR_OK;
+}
+
+// The pixel-centre offsets of one camera, in IEEE double with exactly the
+// operations (and order) of the per-ray formula: s_i = ((i + 0.5) / nx - 0.5)
+// fov0, t_j = ((j + 0.5) / ny - 0.5) fov1.  A row of rays shares t_j and a
+// column s_i, so the kernels read them instead of dividing per ray.
+void pixel_offsets(const CamDev& c, double* out) {
+  for (int i = 0; i < c.nx; ++i) out[i] = (((double)i + 0.5) / c.nxd - 0.5) * c.fov0;
+  for (int j = 0; j < c.ny; ++j) out[c.nx + j] = (((double)j + 0.5) / c.nyd - 0.5) * c.fov1;
+}
+
+// Fill the slot's offset tables for its first n cameras and point them there.
+amr_status fill_offsets(LaunchSlot& s, int n, int64_t* total) {
+  int64_t need = 0;
+  for (int i = 0; i < n; ++i) need += (int64_t)s.h_cams[i].nx + s.h_cams[i].ny;
+  amr_status st = grow_st(s, need);
+  if (st != AMR_OK) return st;
+  int64_t o = 0;
+  for (int i = 0; i < n; ++i) {
+    CamDev& c = s.h_cams[i];
+    pixel_offsets(c, s.h_st + o);
+    c.st = s.d_st + o;
+    o += (int64_t)c.nx + c.ny;
+  }
+  *total = need;
   return AMR_OK;
 }
 
@@ -388,6 +441,9 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   for (int g = 0; g < amr::kMaxPrecisions; ++g) gstart[g + 1] = gstart[g] + groups[g];
   int fill[amr::kMaxPrecisions] = {gstart[0], gstart[1], gstart[2]};
   for (int i = 0; i < n; ++i) s.h_cams[fill[precs[i]]++] = cams[i];
+  int64_t st_total = 0;
+  st = fill_offsets(s, n, &st_total);
+  if (st != AMR_OK) return st;
   int64_t tiles_total[amr::kMaxPrecisions] = {0, 0, 0};
   for (int g = 0; g < amr::kMaxPrecisions; ++g) {
     int32_t* tp = s.h_tiles + (size_t)g * (s.cap + 1);
@@ -437,6 +493,8 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     cudaError_t e = cudaEventRecordWithFlags(s.start, st, ev);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_cams, s.h_cams, n * sizeof(CamDev), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_tiles, s.h_tiles, tile_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.d_st, s.h_st, (size_t)st_total * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), st);
     for (int g = 0; g < amr::kMaxPrecisions && e == cudaSuccess; ++g)
       if (grids[g]) e = amr::launch_batch(g, ctx->tree.f64, args[g], grids[g], opt.block_threads, st);
@@ -449,7 +507,8 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   if (opt.use_graph) {
     // Replay a captured graph of this slot when the batch shape is unchanged
     // (the camera table itself is read from the slot's pinned staging).
-    std::vector<int64_t> key = {n, s.cap, (int64_t)(uintptr_t)s.d_cams, (int64_t)(uintptr_t)ctx->tree.rec,
+    std::vector<int64_t> key = {n, s.cap, (int64_t)(uintptr_t)s.d_cams, st_total, (int64_t)(uintptr_t)s.d_st,
+                                (int64_t)(uintptr_t)ctx->tree.rec,
                                 (int64_t)(uintptr_t)ctx->tree.nbr, ctx->tree.f64, opt.block_threads,
                                 opt.tile_w, opt.tile_h, opt.tiles_per_grab};
     for (int g = 0; g < amr::kMaxPrecisions; ++g) {
@@ -485,6 +544,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   s.pending = true;
   ctx->n_renders++;
   ctx->n_cams += n;
+  ctx->n_h2d_bytes += (int64_t)(n * sizeof(CamDev) + tile_bytes) + st_total * (int64_t)sizeof(double);
   for (const CamDev& c : cams) ctx->n_rays += (int64_t)c.nx * c.ny;
   if (used) *used = &s;
   return AMR_OK;
@@ -501,9 +561,14 @@ amr_status enqueue_slice(amr_ctx* ctx, const CamDev& cam, bool out64, cudaStream
     harvest(ctx, s);
   }
   s.h_cams[0] = cam;
+  int64_t st_total = 0;
+  amr_status st = fill_offsets(s, 1, &st_total);
+  if (st != AMR_OK) return st;
   s.n_groups = amr::kMaxPrecisions;
   CUDA_TRY(cudaEventRecord(s.start, stream));
   CUDA_TRY(cudaMemcpyAsync(s.d_cams, s.h_cams, sizeof(CamDev), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_st, s.h_st, (size_t)st_total * sizeof(double), cudaMemcpyHostToDevice, stream));
+  ctx->n_h2d_bytes += (int64_t)sizeof(CamDev) + st_total * (int64_t)sizeof(double);
   CUDA_TRY(cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), stream));
   CUDA_TRY(amr::launch_slice(out64, ctx->tree.f64, ctx->tree.rec, (uint32_t)ctx->tree.n_oct, s.d_cams,
                              (int64_t)cam.nx * cam.ny, &s.d_q[0].error, stream));
@@ -1291,7 +1356,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
   char buf[2048];
   int len = std::snprintf(
       buf, sizeof buf,
-      "{\"renders\": %lld, \"cameras\": %lld, \"rays\": %lld, \"segments\": %llu, \"device_errors\": %lld, "
+      "{\"renders\": %lld, \"cameras\": %lld, \"rays\": %lld, \"segments\": %llu, \"h2d_bytes\": %lld, \"device_errors\": %lld, "
       "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d}, "
       "\"options\": {\"tile_w\": %d, \"tile_h\": %d, \"block_threads\": %d, \"blocks_per_sm\": %d, "
       "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
@@ -1299,7 +1364,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       "\"server\": {\"done\": %lld, \"failed\": %lld, \"batches\": %lld, \"max_inflight\": %lld, \"queued\": %lld, "
       "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
-      (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
+      (long long)ctx->n_h2d_bytes, (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
       (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
       o.use_graph, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,

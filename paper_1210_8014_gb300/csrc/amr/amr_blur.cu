@@ -35,14 +35,21 @@ __global__ void __launch_bounds__(256) blur_pass(const float* __restrict__ in, c
   }
   const int R = min(kMaxRadius, (int)(3.0f * sg + 0.5f));
   const float g = -0.5f / (sg * sg);
-  float acc = 0.0f, norm = 0.0f;
-  for (int k = -R; k <= R; ++k) {
-    const int xx = COLUMNS ? x : x + k;
-    const int yy = COLUMNS ? y + k : y;
-    if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) continue;
+  // The centre tap, then the pairs at +-k sharing one weight (one exponential
+  // per pair: the special-function unit is this pass's narrowest resource).
+  const int pos = COLUMNS ? y : x, len = COLUMNS ? ny : nx;
+  const size_t stride = COLUMNS ? (size_t)nx : 1;
+  float acc = __ldg(&in[p]), norm = 1.0f;
+  for (int k = 1; k <= R; ++k) {
     const float wgt = __expf(g * (float)(k * k));
-    acc = fmaf(wgt, __ldg(&in[(size_t)yy * nx + xx]), acc);
-    norm += wgt;
+    if (pos - k >= 0) {
+      acc = fmaf(wgt, __ldg(&in[p - k * stride]), acc);
+      norm += wgt;
+    }
+    if (pos + k < len) {
+      acc = fmaf(wgt, __ldg(&in[p + k * stride]), acc);
+      norm += wgt;
+    }
   }
   out[p] = acc / norm;
 }

@@ -50,6 +50,11 @@ struct CamDev {
   const void* vel[3];       // wmean velocity fields
   void* map;                // float* or double* [ny][nx]
   int32_t* counts;          // nullable
+  // Pixel-centre offsets, [nx + ny] doubles: s_i = ((i + 0.5) / nx - 0.5) fov0
+  // for i < nx, then t_j likewise with ny and fov1, each rounded exactly as the
+  // per-ray formula would; filled on the host per launch.  Null: the kernels
+  // evaluate the formula per ray.
+  const double* st;
 };
 
 // Scratch block one launch owns: queue head, error word, segment counter.

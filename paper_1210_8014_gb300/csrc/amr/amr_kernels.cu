@@ -69,8 +69,16 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   RayOut res{0.0, 0.0f, 0};
 
   // ---- ray set-up: FP64 pixel centre, quantised origin ----------------------
-  const double s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
-  const double t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+  // The offsets along u and v come from the launch's per-camera table (the
+  // same IEEE operations, done once per column and row) when there is one.
+  double s, t;
+  if (cam.st) {
+    s = __ldg(cam.st + i);
+    t = __ldg(cam.st + cam.nx + j);
+  } else {
+    s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
+    t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+  }
   long long X[3];
   int D[3], aD[3];
 #pragma unroll

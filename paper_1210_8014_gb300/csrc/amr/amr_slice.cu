@@ -20,8 +20,14 @@ __global__ void __launch_bounds__(256) slice_kernel(const uint2* __restrict__ re
   const int64_t px = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (px >= (int64_t)cam.nx * cam.ny) return;
   const int i = (int)(px % cam.nx), j = (int)(px / cam.nx);
-  const double s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
-  const double t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+  double s, t;
+  if (cam.st) {  // per-camera table of the same offsets
+    s = __ldg(cam.st + i);
+    t = __ldg(cam.st + cam.nx + j);
+  } else {
+    s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
+    t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+  }
   long long X[3];
   bool inside = true;
 #pragma unroll
