@@ -7,8 +7,9 @@
 //
 // Per ray:
 //   set-up  : pixel centre in IEEE double (the only FP64 step of the FP32
-//             kernels), rounded to the 2^-36 lattice; box entry by exact
-//             comparisons of rational crossing times.
+//             kernels) from the camera's per-column and per-row offsets,
+//             rounded to the 2^-36 lattice; box entry by exact comparisons of
+//             rational crossing times.
 //   descent : from the root down to the leaf holding the ray (Sec. 2.2),
 //             choosing children by the exact side of the mid-planes at the
 //             entry time; stops at a leaf or at the camera's level (Sec. 2).
@@ -18,6 +19,8 @@
 //             the next cell is the same oct's neighbour (a bit flip of the
 //             cell index) or the oct named by a face link (a coarser leaf, or
 //             the end of the box); refined neighbours are descended into.
+//             Per-camera tables indexed by the (entry, exit) axes and by the
+//             set of stepped axes replace per-axis selects on this path.
 //             Without links (the no-allocation entry point) the neighbour is
 //             reached through the stack of ancestor octs instead.
 //
@@ -214,8 +217,6 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   float Sf = 0.0f, cSf = 0.0f, Nf = 0.0f, cNf = 0.0f, Mf = 0.0f;
   int count = 0;
 
-  // Every step moves on at least one axis (the exit-face test always selects
-  // one), so the loop ends; the cap only guards against a corrupted tree.
   // With links the step keeps only (o, c); the cell's integer coordinates are
   // rebuilt from the oct's packed corner (after its six links) where a level
   // change or a corner needs them.
@@ -225,6 +226,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     k1 = (int)(((pk >> 21) & 0x1FFFFFull) << 1) | ((c >> 1) & 1);
     k2 = (int)(((pk >> 42) & 0x1FFFFFull) << 1) | ((c >> 2) & 1);
   };
+  // Every step moves on at least one axis (the exit-face test always selects
+  // one), so the loop ends; the cap only guards against a corrupted tree.
   while (count < kStepCap) {
     const size_t cell = (size_t)o * 8 + c;
     const F rho = load_field<F>(rho_base, cell);
@@ -248,13 +251,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       //   (K - 1) s + (s - r),  K = |D_b| - E,  when ea < b  (e' = e),
       //    K s + r,             K = |D_b| + E,  when ea > b  (e' = -e),
       // two non-negative parts (K >= 1, resp. K >= 0, since the chord is > 0).
-      //   (t_exit - t_entry) = s / |D_b|                      (b == ea)
-      // The same axis twice (b == ea) gives s / |D_b|, written as K = |D_b|
-      // with no remainder part.  The camera's record for (ea, b) holds K's
-      // offset and sign, the factor and where the remainder part is: the step
-      // needs no per-axis selects.
-      // z E is picked out of (F01, F02, F12) by multiply-adds (FMA pipe)
-      // instead of compares and selects (ALU pipe).
+      // The same axis twice (b == ea) gives (t_exit - t_entry) = s / |D_b|,
+      // written as K = |D_b| with no remainder part.  The camera's records for
+      // (ea, b) hold K's offset, the factor, where the remainder part is, and
+      // selectors that pick z E out of (F01, F02, F12) by multiply-adds (FMA
+      // pipe) instead of compares and selects (ALU pipe).
       const int4 pc = __ldg(&cam.chord[ea][b]);
       const int4 ps = __ldg(&cam.chordsel[ea][b]);
       const int K = pc.y + ((F01 * ps.x + F02 * ps.y + F12 * ps.z + ps.w) >> 1);
