@@ -10,9 +10,18 @@ The paper distributes the octree among processes, each rendering its own part
            (each domain renders column maps of rho and rho*v_x, rho*v_y,
            rho*v_z, so a weighted mean merges from sums alone)
 
-Each domain keeps the whole tree structure and zeroes the values of leaves it
-does not own, so every domain traverses the same cells: per-pixel counts are
-identical across domains and are checked, not added.
+Two forms of a domain's tree:
+  domain_tree     the whole structure with the values of cells it does not own
+                  zeroed: every domain traverses the same cells, so per-pixel
+                  counts are identical across domains and are checked, not added;
+  domain_subtree  only what the domain needs, for trees too large for one
+                  device: the octs above its own cells, foreign subtrees cut
+                  back to zero-valued leaves (and one level of zero-valued
+                  children under an owned refined cell whose descendants are all
+                  foreign, so cuts below that cell still read zeros there).
+                  Partial maps merge exactly as before; counts are per domain
+                  (they include the zero-valued cells it crosses) and are not
+                  merged.
 
 The domain split is spatial: leaves sorted by the Morton key of their centre
 (at level 22) and cut into contiguous key ranges of equal leaf count.
@@ -63,16 +72,69 @@ def domain_tree(tree: Tree, owner: np.ndarray, d: int, with_momentum: bool = Fal
     """The tree with the values of cells outside domain d set to zero.  With
     with_momentum, fields become [rho, rho*v_x, rho*v_y, rho*v_z] (the column
     fields a weighted-mean merge needs)."""
-    mine = owner == d
-    rho = np.where(mine, tree.fields[0], 0)
-    fields = [rho.astype(tree.fields[0].dtype)]
+    return replace(tree, fields=_fields_for(tree, owner == d, with_momentum))
+
+
+def _fields_for(tree: Tree, mine: np.ndarray, with_momentum: bool) -> list:
+    rho = np.where(mine, tree.fields[0], 0).astype(tree.fields[0].dtype)
+    out = [rho]
     if with_momentum:
         for a in (1, 2, 3):
-            fields.append(np.where(mine, tree.fields[0].astype(np.float64) * tree.fields[a], 0)
-                          .astype(tree.fields[0].dtype))
+            out.append(np.where(mine, tree.fields[0].astype(np.float64) * tree.fields[a], 0)
+                       .astype(tree.fields[0].dtype))
     else:
-        fields += [np.where(mine, f, 0).astype(f.dtype) for f in tree.fields[1:]]
-    return replace(tree, fields=fields)
+        out += [np.where(mine, f, 0).astype(f.dtype) for f in tree.fields[1:]]
+    return out
+
+
+def domain_subtree(tree: Tree, owner: np.ndarray, d: int, with_momentum: bool = False) -> Tree:
+    """The pruned tree of domain d (see the module docstring): keeps oct o when
+    its subtree holds a cell owned by d, or when o refines a cell owned by d
+    (then, if nothing below o is owned by d, o is kept as zero-valued leaves).
+    Values of cells not owned by d are zero.  The root is always kept."""
+    n = tree.n_oct
+    owned = owner == d
+    child = tree.child
+    level = tree.level.astype(np.int64)
+    # sub[o]: the subtree of oct o holds a cell owned by d (children are deeper,
+    # so one sweep from the deepest level up settles every oct)
+    sub = owned.any(axis=1)
+    for lv in range(int(level.max()), 0, -1):
+        octs = np.nonzero(level == lv)[0]
+        ch = child[octs]
+        has = ch >= 0
+        if has.any():
+            hit = np.zeros(ch.shape, bool)
+            hit[has] = sub[ch[has]]
+            sub[octs] |= hit.any(axis=1)
+    keep = np.zeros(n, bool)
+    leafify = np.zeros(n, bool)          # kept with every cell a zero leaf
+    keep[0] = True
+    for lv in range(1, int(level.max()) + 1):
+        octs = np.nonzero((level == lv) & keep & ~leafify)[0]
+        ch = child[octs]
+        has = ch >= 0
+        if not has.any():
+            continue
+        c_oct = ch[has]
+        c_owned = owned[octs][has]
+        into = sub[c_oct]
+        keep[c_oct[into]] = True
+        zero = ~into & c_owned
+        keep[c_oct[zero]] = True
+        leafify[c_oct[zero]] = True
+    old = np.nonzero(keep)[0]
+    new_index = np.full(n, -1, np.int64)
+    new_index[old] = np.arange(old.size)
+    ch = child[old]
+    nc = np.where(ch >= 0, new_index[np.maximum(ch, 0)], -1)
+    nc[leafify[old]] = -1
+    mine = owned[old] & ~leafify[old][:, None]
+    sub_tree = Tree(level=tree.level[old].copy(), coord=tree.coord[old].copy(), child=nc.astype(np.int32),
+                    fields=[], info=dict(tree.info))
+    base = Tree(level=sub_tree.level, coord=sub_tree.coord, child=sub_tree.child,
+                fields=[np.asarray(f)[old] for f in tree.fields], info=sub_tree.info)
+    return replace(sub_tree, fields=_fields_for(base, mine, with_momentum))
 
 
 def partial_cameras(cam: Camera) -> list[Camera]:

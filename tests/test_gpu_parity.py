@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 import oracle_pins
-from parity import assert_parity, errors
+from parity import TOL, assert_parity, errors
 from paper_1210_8014_gb300 import amr, inputs
 
 pytestmark = pytest.mark.gpu
@@ -392,6 +392,40 @@ def test_sortlast_domains_rendered_in_turn(gpu):
         wm, wc = whole[q]
         assert (mc == wc).all()
         assert_parity(cam.mode, 1, merged, mc, wm.astype(np.float64), wc, ctx=f"sort-last camera {q}")
+
+
+def test_sortlast_pruned_subtrees_rendered_in_turn(gpu):
+    """Sort-last with pruned per-domain trees (each holds about a quarter of the
+    octs): partial maps rendered in turn on the GPU merge into the whole-tree
+    GPU render, at the pixel-rule cut and at coarser cuts."""
+    from paper_1210_8014_gb300 import sortlast
+    tree = tree_of("galaxy")
+    own = sortlast.domain_owner(tree, 4)
+    base = [c.with_(precision=amr.AMR_PREC_FP32_KAHAN) for c in mixed_batch(tree, 4, seed=41)]
+    cams = base + [c.with_(max_level=L) for c in base[:2] for L in (8, 10)]
+    with amr.Renderer(tree) as r:
+        whole = [host(m) for m, _ in r.render_batch(cams)]
+    parts = {q: [] for q in range(len(cams))}
+    for d in range(4):
+        for mom in (False, True):
+            sub = [q for q, c in enumerate(cams) if (c.mode == 1) == mom]
+            if not sub:
+                continue
+            st = sortlast.domain_subtree(tree, own, d, with_momentum=mom)
+            assert st.n_oct < 0.3 * tree.n_oct
+            with amr.Renderer(st) as r:
+                for q in sub:
+                    outs = r.render_batch(sortlast.partial_cameras(cams[q]))
+                    parts[q].append([host(m) for m, _ in outs])
+    for q, cam in enumerate(cams):
+        merged, _ = sortlast.merge(cam, parts[q])
+        wm = whole[q].astype(np.float64)
+        if cam.mode == 2:
+            assert (merged == wm).all(), q
+        else:
+            # the FP32-compensated tolerance, per pixel for columns, normwise for wmean
+            e = errors(cam.mode, merged, wm)
+            assert e["zero_ok"] and e["max"] <= TOL[1], (q, e)
 
 
 def test_slice_map_matches_oracle(gpu):

@@ -60,6 +60,85 @@ def test_merged_partials_equal_whole_render(n_domains):
             assert np.abs(merged - whole).max() <= 1e-12 * np.abs(whole).max()
 
 
+def _check_tree(t):
+    """What amr_load_octree validates: root at index 0, level 1, coordinate 0;
+    each child one level deeper at twice its parent cell's coordinates; every
+    non-root oct referenced exactly once."""
+    assert t.level[0] == 1 and (t.coord[0] == 0).all()
+    refs = np.zeros(t.n_oct, np.int64)
+    o, c = np.nonzero(t.child >= 0)
+    ch = t.child[o, c]
+    np.add.at(refs, ch, 1)
+    assert refs[0] == 0 and (refs[1:] == 1).all()
+    assert (t.level[ch] == t.level[o] + 1).all()
+    off = np.stack([(c >> a) & 1 for a in range(3)], axis=1)
+    assert (t.coord[ch] == 2 * (t.coord[o] + off)).all()
+
+
+def test_subtrees_are_valid_and_split_the_tree():
+    tree = small_galaxy()
+    for n in (2, 4, 7):
+        own = sortlast.domain_owner(tree, n)
+        sizes = []
+        for d in range(n):
+            st = sortlast.domain_subtree(tree, own, d)
+            _check_tree(st)
+            sizes.append(st.n_oct)
+            # every owned value survives; nothing else is nonzero
+            assert np.isclose(float(st.fields[0].sum()), float(tree.fields[0][own == d].sum()), rtol=1e-12)
+        # the domains together hold the tree once plus shared ancestors
+        assert sum(sizes) < tree.n_oct * 1.25 and max(sizes) < tree.n_oct / n * 1.3
+
+
+@pytest.mark.parametrize("n_domains", [2, 4])
+def test_merged_subtree_partials_equal_whole_render(n_domains):
+    """Pruned per-domain trees merge into the whole render at the pixel-rule
+    cut and at cuts above the finest level (where owned refined cells read as
+    leaves and foreign ones as zeros)."""
+    tree = small_galaxy()
+    own = sortlast.domain_owner(tree, n_domains)
+    cams = cams_for(tree) + [c.with_(max_level=L) for c in cams_for(tree) for L in (5, 7)]
+    subs = {(d, mom): sortlast.domain_subtree(tree, own, d, with_momentum=mom)
+            for d in range(n_domains) for mom in (False, True)}
+    for cam in cams:
+        whole, _ = oracle.render(tree, cam)
+        parts = []
+        for d in range(n_domains):
+            st = subs[(d, cam.mode == 1)]
+            parts.append([oracle.render(st, pc)[0] for pc in sortlast.partial_cameras(cam)])
+        merged, mc = sortlast.merge(cam, parts)
+        assert mc is None
+        if cam.mode == 2:
+            assert (merged == whole).all()
+        elif cam.mode == 0:
+            assert np.abs(merged - whole).max() <= 1e-13 * np.abs(whole).max()
+        else:
+            assert np.abs(merged - whole).max() <= 1e-12 * np.abs(whole).max()
+
+
+def test_subtree_owned_refined_cell_with_foreign_descendants():
+    """Refined cells owned by another domain than their descendants (random
+    owners for refined cells): the owner keeps one level of zero-valued children
+    under each such cell, so cuts below it still read zeros there.  Without
+    that level the merge is off by percents at cuts 7 and the pixel rule."""
+    tree = small_galaxy()
+    own = sortlast.domain_owner(tree, 3)
+    refined = tree.child >= 0
+    own[refined] = np.random.default_rng(3).integers(0, 3, int(refined.sum()))
+    subs = [sortlast.domain_subtree(tree, own, d) for d in range(3)]
+    for st in subs:
+        _check_tree(st)
+    for cam in [c for c in cams_for(tree) if c.mode != 1]:
+        for L in (5, 7, -1):
+            c = cam.with_(max_level=L)
+            whole, _ = oracle.render(tree, c)
+            merged, _ = sortlast.merge(c, [[oracle.render(st, c)[0]] for st in subs])
+            if c.mode == 2:
+                assert (merged == whole).all()
+            else:
+                assert np.abs(merged - whole).max() <= 1e-13 * np.abs(whole).max()
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
