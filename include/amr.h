@@ -103,7 +103,8 @@ amr_status amr_create(amr_ctx** out, int device);
 amr_status amr_destroy(amr_ctx* ctx);
 
 /*
- * Load (replace) the octree.  Host arrays, n_oct octs:
+ * Load (replace) the octree.  Host arrays, n_oct octs (1 <= n_oct <= (2^31 - 1) / 8,
+ * else AMR_E_INVALID: cell indices oct * 8 + c are 32-bit in the kernels):
  *   level[n_oct]        uint8, root = oct 0 at level 1, levels <= 22
  *   coord[n_oct][3]     int32 corner of the oct's cell 0 in level-l cell units (even)
  *   child[n_oct][8]     int32 oct refining cell c, or -1 (leaf)
@@ -216,6 +217,7 @@ amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket);
  * and the launch scratch (camera table, tile prefix sums, work-queue head) lives
  * in a fixed library-owned device array of under 224 KiB that every GPU loading
  * this library holds until exit.
+ *   n_oct     1 <= n_oct <= (2^31 - 1) / 8 (AMR_E_INVALID otherwise)
  *   records   device, [n_oct] uint64: bits 0-31 index of the oct's first child
  *             oct, bits 32-39 its refinement mask (bit c set: cell c refined).
  *             Octs breadth-first from the root (index 0, level 1), the children

@@ -229,7 +229,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   // Every step moves on at least one axis (the exit-face test always selects
   // one), so the loop ends; the cap only guards against a corrupted tree.
   while (count < kStepCap) {
-    const size_t cell = (size_t)o * 8 + c;
+    // 32-bit cell and link indices (n_oct * 8 < 2^31 is checked at load): one
+    // 32 x 32 -> 64-bit multiply-add per address instead of 64-bit arithmetic.
+    const uint32_t cell = o * 8u + (uint32_t)c;
     const F rho = load_field<F>(rho_base, cell);
 
     // Exit face(s): the axes whose exit time is the minimum.
@@ -310,7 +312,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         // that side, or -1 where the box ends.  The common case (a same-level
         // oct) runs as predicated loads, no branch.
         int v = (int)o;
-        if (!inoct) v = __ldg(&A.nbr[(size_t)o * 8 + (dF.w & 7)]);
+        if (!inoct) v = __ldg(&A.nbr[o * 8u + (uint32_t)(dF.w & 7)]);
         if (v >= 0) {
           if ((uint32_t)v >= A.n_oct) { bad = true; break; }
           if (!inoct) r = __ldg(&rec[v]);
