@@ -1120,6 +1120,17 @@ amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t
     d.counts = level_out;
     return enqueue_slice(ctx, d, out64, stream, &s);
   }
+  // Page-locked host outputs the GPU can address are written in place.
+  void* hm = host_alias(map_out);
+  void* hl = level_out ? host_alias(level_out) : nullptr;
+  if (hm && (hl || !level_out)) {
+    d.map = hm;
+    d.counts = (int32_t*)hl;
+    st = enqueue_slice(ctx, d, out64, stream, &s);
+    if (st != AMR_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return finish_sync(ctx, s);
+  }
   const int64_t moff = ((mbytes + 255) / 256) * 256;
   st = ensure_stage(ctx, moff + (level_out ? px * 4 : 0));
   if (st != AMR_OK) return st;

@@ -446,6 +446,11 @@ def test_slice_map_matches_oracle(gpu):
             m64 = np.zeros((cam.ny, cam.nx), np.float64)
             amr.amr_slice(r.ctx, cam.with_(precision=amr.AMR_PREC_FP64), m64, None, 0)
             assert (m64 == ref).all(), k
+            # page-locked host outputs are written in place
+            mp = torch.full((cam.ny, cam.nx), float("nan"), dtype=torch.float32, pin_memory=True).numpy()
+            lp = torch.full((cam.ny, cam.nx), -1, dtype=torch.int32, pin_memory=True).numpy()
+            amr.amr_slice(r.ctx, cam.with_(precision=amr.AMR_PREC_FP32_KAHAN), mp, lp, 0)
+            assert (lp == rl).all() and (mp.astype(np.float64) == ref).all(), k
 
 
 def test_mean_level_and_adaptive_blur(gpu):
