@@ -44,7 +44,7 @@ BYTES_PER_SEG = {0: 8, 1: 20, 2: 8}   # child word + scalars per segment, float3
 OPS_PER_SEG = {0: 30, 1: 43, 2: 21}
 # 152 SMs x 128 lanes x 2.07 GHz: one lane operation per lane per clock.
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-FP64_OPS_PER_SEG = 6       # int64->f64, two multiplies for the chord, float->double, multiply, add
+FP64_OPS_PER_SEG = 5       # int64->f64, the chord's multiply by the per-camera factor, float->double, multiply, add
 FP64_PEAK_TFLOPS = 1.25    # nominal GB300 FP64 rate
 
 
