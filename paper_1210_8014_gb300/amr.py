@@ -115,6 +115,46 @@ def _ptr(x) -> Optional[int]:
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+def _buf(x, n: int, itemsize: int, kind: str, where: Optional[str], name: str) -> Optional[int]:
+    """Pointer of a buffer a call reads or writes, after checking what the C
+    call will touch (the library cannot): at least n elements of itemsize
+    bytes of the right kind ('f' float, 'i' integer), contiguous, on the
+    expected side ('device', 'host', or None for either).  Raw integer
+    pointers pass unchecked."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        is_float, count, size, dev = x.is_floating_point(), x.numel(), x.element_size(), x.is_cuda
+        contiguous = x.is_contiguous()
+        ptr = x.data_ptr
+    elif isinstance(x, np.ndarray):
+        is_float, count, size, dev = x.dtype.kind == "f", x.size, x.itemsize, False
+        contiguous = x.flags.c_contiguous
+        ptr = lambda: x.ctypes.data
+    else:
+        raise TypeError(f"{name}: cannot take a pointer of {type(x)}")
+    if not contiguous:
+        raise ValueError(f"{name}: buffer is not contiguous")
+    if is_float != (kind == "f") or size != itemsize:
+        want = {("f", 4): "float32", ("f", 8): "float64", ("i", 4): "int32"}[(kind, itemsize)]
+        raise ValueError(f"{name}: need {want} elements")
+    if count < n:
+        raise ValueError(f"{name}: {count} elements, need {n}")
+    if where == "device" and not dev:
+        raise ValueError(f"{name}: a host buffer where a device buffer is needed")
+    if where == "host" and dev:
+        raise ValueError(f"{name}: a device buffer where a host buffer is needed")
+    return ptr()
+
+
+def _map_size(cam: Camera) -> int:
+    return 8 if int(cam.precision) == AMR_PREC_FP64 else 4
+
+
+def _side(out_on_device) -> str:
+    return "device" if out_on_device else "host"
+
+
 def to_camera(cam: Camera) -> amr_camera:
     c = amr_camera()
     for name in ("centre", "u", "v", "w"):
@@ -146,28 +186,43 @@ def amr_load_octree(ctx, n_oct, level, coord, child, fields: Sequence, field_dty
 
 def amr_render(ctx, cam: Camera, map_out, count_out=None, out_on_device: int = 1, cuda_stream=None) -> None:
     c = to_camera(cam)
-    _check(lib().amr_render(ctx, ctypes.byref(c), _ptr(map_out), _ptr(count_out), int(out_on_device),
+    px, side = int(cam.nx) * int(cam.ny), _side(out_on_device)
+    m = _buf(map_out, px, _map_size(cam), "f", side, "map_out")
+    k = _buf(count_out, px, 4, "i", side, "count_out")
+    _check(lib().amr_render(ctx, ctypes.byref(c), m, k, int(out_on_device),
                             _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 def amr_render_batch(ctx, cams: Sequence[Camera], maps: Sequence, counts: Optional[Sequence] = None,
                      out_on_device: int = 1, cuda_stream=None) -> None:
     n = len(cams)
+    if len(maps) != n or (counts is not None and len(counts) != n):
+        raise ValueError("one map (and one counts entry, if counts are given) per camera")
     carr = (amr_camera * n)(*[to_camera(c) for c in cams])
-    marr = (ctypes.c_void_p * n)(*[_ptr(m) for m in maps])
-    karr = (ctypes.c_void_p * n)(*[_ptr(k) for k in counts]) if counts is not None else None
+    side = _side(out_on_device)
+    marr = (ctypes.c_void_p * n)(*[_buf(m, int(c.nx) * int(c.ny), _map_size(c), "f", side, f"maps[{i}]")
+                                   for i, (m, c) in enumerate(zip(maps, cams))])
+    karr = (ctypes.c_void_p * n)(*[_buf(k, int(c.nx) * int(c.ny), 4, "i", side, f"counts[{i}]")
+                                   for i, (k, c) in enumerate(zip(counts, cams))]) if counts is not None else None
     _check(lib().amr_render_batch(ctx, n, carr, marr, karr, int(out_on_device),
                                   _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 def amr_slice(ctx, cam: Camera, map_out, level_out=None, out_on_device: int = 1, cuda_stream=None) -> None:
     c = to_camera(cam)
-    _check(lib().amr_slice(ctx, ctypes.byref(c), _ptr(map_out), _ptr(level_out), int(out_on_device),
+    px, side = int(cam.nx) * int(cam.ny), _side(out_on_device)
+    m = _buf(map_out, px, _map_size(cam), "f", side, "map_out")
+    lv = _buf(level_out, px, 4, "i", side, "level_out")
+    _check(lib().amr_slice(ctx, ctypes.byref(c), m, lv, int(out_on_device),
                            _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 def amr_blur(ctx, nx: int, ny: int, map_in, level, pixel: float, map_out, cuda_stream=None) -> None:
-    _check(lib().amr_blur(ctx, int(nx), int(ny), _ptr(map_in), _ptr(level), float(pixel), _ptr(map_out),
+    px = int(nx) * int(ny)
+    a = _buf(map_in, px, 4, "f", "device", "map_in")
+    lv = _buf(level, px, 4, "f", "device", "level")
+    b = _buf(map_out, px, 4, "f", "device", "map_out")
+    _check(lib().amr_blur(ctx, int(nx), int(ny), a, lv, float(pixel), b,
                           _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
@@ -205,7 +260,10 @@ def amr_server_config(ctx, slots: int = 2, map_budget_bytes: int = 0, max_batch:
 
 def amr_submit(ctx, cam: Camera, map_host, counts_host=None) -> int:
     t = ctypes.c_uint64()
-    _check(lib().amr_submit(ctx, ctypes.byref(to_camera(cam)), _ptr(map_host), _ptr(counts_host), ctypes.byref(t)))
+    px = int(cam.nx) * int(cam.ny)
+    m = _buf(map_host, px, _map_size(cam), "f", "host", "map_host")
+    k = _buf(counts_host, px, 4, "i", "host", "counts_host")
+    _check(lib().amr_submit(ctx, ctypes.byref(to_camera(cam)), m, k, ctypes.byref(t)))
     return int(t.value)
 
 
@@ -237,11 +295,16 @@ def amr_render_batch_noalloc(n_oct: int, records, depth: int, fields: Sequence, 
                              cuda_stream=None) -> None:
     """Batch render with no GPU allocation: tree, maps and counts are the caller's device buffers."""
     n = len(cams)
-    farr = (ctypes.c_void_p * len(fields))(*[_ptr(f) for f in fields])
+    fsize = 8 if int(field_dtype) == AMR_F64 else 4
+    farr = (ctypes.c_void_p * len(fields))(*[_buf(f, int(n_oct) * 8, fsize, "f", "device", f"fields[{i}]")
+                                             for i, f in enumerate(fields)])
     carr = (amr_camera * max(n, 1))(*[to_camera(c) for c in cams])
-    marr = (ctypes.c_void_p * max(n, 1))(*[_ptr(m) for m in maps])
-    karr = (ctypes.c_void_p * max(n, 1))(*[_ptr(k) for k in counts]) if counts is not None else None
-    _check(lib().amr_render_batch_noalloc(int(n_oct), _ptr(records), int(depth), len(fields), farr, int(field_dtype),
+    marr = (ctypes.c_void_p * max(n, 1))(*[_buf(m, int(c.nx) * int(c.ny), _map_size(c), "f", "device", f"maps[{i}]")
+                                           for i, (m, c) in enumerate(zip(maps, cams))])
+    karr = (ctypes.c_void_p * max(n, 1))(*[_buf(k, int(c.nx) * int(c.ny), 4, "i", "device", f"counts[{i}]")
+                                           for i, (k, c) in enumerate(zip(counts, cams))]) if counts is not None else None
+    recs = _buf(records, int(n_oct), 8, "i", "device", "records")
+    _check(lib().amr_render_batch_noalloc(int(n_oct), recs, int(depth), len(fields), farr, int(field_dtype),
                                           n, carr, marr, karr, _ptr(cuda_stream) if cuda_stream is not None else None))
 
 

@@ -58,3 +58,38 @@ def test_calls_fail_cleanly_without_a_device():
     assert L.amr_render_batch(None, 1, None, None, None, 1, None) == amr.AMR_E_INVALID
     assert L.amr_destroy(None) == amr.AMR_OK
     assert L.amr_stats(None, None, 0) == amr.AMR_E_INVALID
+
+
+def test_binding_checks_buffers_before_the_call():
+    """The library cannot see buffer sizes; the binding checks what a call will
+    touch (length, element type, contiguity, host or device side) and raises
+    before any native call (ctx None: nothing reaches the library)."""
+    import numpy as np
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+    cam = inputs.axis_camera(16, max_level=3, precision=amr.AMR_PREC_FP32_KAHAN)
+    ok_map, ok_cnt = np.zeros((16, 16), np.float32), np.zeros((16, 16), np.int32)
+    bad = [
+        ((np.zeros(100, np.float32), ok_cnt), "elements, need 256"),        # too short
+        ((np.zeros((16, 16), np.float64), ok_cnt), "need float32"),         # FP32 map given doubles
+        ((np.zeros((16, 16), np.int32), ok_cnt), "need float32"),           # integers for a map
+        ((ok_map, np.zeros((16, 16), np.float32)), "need int32"),           # floats for counts
+        ((np.zeros((16, 32), np.float32)[:, ::2], ok_cnt), "not contiguous"),
+    ]
+    for (m, c), msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            amr.amr_render(None, cam, m, c, 0)
+    with pytest.raises(ValueError, match="device buffer is needed"):
+        amr.amr_render(None, cam, ok_map, ok_cnt, 1)                        # host arrays, device outputs
+    with pytest.raises(ValueError, match="need float64"):
+        amr.amr_render(None, cam.with_(precision=amr.AMR_PREC_FP64), ok_map, None, 0)
+    with pytest.raises(ValueError, match="one map"):
+        amr.amr_render_batch(None, [cam, cam], [ok_map], None, 0)
+    with pytest.raises(ValueError, match=r"maps\[1\]"):
+        amr.amr_render_batch(None, [cam, cam.with_(nx=32)], [ok_map, ok_map], None, 0)
+    with pytest.raises(ValueError, match="need int32"):
+        amr.amr_slice(None, cam, ok_map, np.zeros((16, 16), np.float32), 0)
+    with pytest.raises(ValueError, match="device buffer is needed"):
+        amr.amr_blur(None, 16, 16, ok_map, ok_map, 0.1, ok_map)
+    with pytest.raises(ValueError, match="elements, need 256"):
+        amr.amr_submit(None, cam, torch.zeros(10), None)

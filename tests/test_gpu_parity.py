@@ -504,8 +504,9 @@ def test_server_timeout_cancel_budget_and_shutdown(gpu):
         ref, rc = r.render(big)
         assert (bufs[0][0] == host(ref)).all() and (bufs[2][1] == host(rc)).all()
         huge = big.with_(nx=8192, ny=8192)                # 512 MiB of map: over the 40 MiB budget
-        with pytest.raises(amr.AmrError) as e:
-            amr.amr_submit(r.ctx, huge, np.zeros(1, np.float32))
+        tiny_buf = np.zeros(1, np.float32)                # refused at submit, before anything is written;
+        with pytest.raises(amr.AmrError) as e:             # a raw pointer skips the binding's size check
+            amr.amr_submit(r.ctx, huge, tiny_buf.ctypes.data)
         assert e.value.status == amr.AMR_E_OOM
         st = r.stats()["server"]
         assert st["done"] == 3 and st["queued"] == 0
