@@ -136,7 +136,7 @@ def _buf(x, n: int, itemsize: int, kind: str, where: Optional[str], name: str) -
     if not contiguous:
         raise ValueError(f"{name}: buffer is not contiguous")
     if is_float != (kind == "f") or size != itemsize:
-        want = {("f", 4): "float32", ("f", 8): "float64", ("i", 4): "int32"}[(kind, itemsize)]
+        want = ("float" if kind == "f" else "int") + str(8 * itemsize)
         raise ValueError(f"{name}: need {want} elements")
     if count < n:
         raise ValueError(f"{name}: {count} elements, need {n}")
@@ -179,9 +179,13 @@ def amr_destroy(ctx) -> None:
 
 
 def amr_load_octree(ctx, n_oct, level, coord, child, fields: Sequence, field_dtype: int) -> None:
-    ptrs = (ctypes.c_void_p * len(fields))(*[_ptr(f) for f in fields])
-    _check(lib().amr_load_octree(ctx, int(n_oct), _ptr(level), _ptr(coord), _ptr(child), len(fields), ptrs,
-                                 int(field_dtype)))
+    n = int(n_oct)
+    fsize = 8 if int(field_dtype) == AMR_F64 else 4
+    ptrs = (ctypes.c_void_p * len(fields))(*[_buf(f, n * 8, fsize, "f", "host", f"fields[{i}]")
+                                             for i, f in enumerate(fields)])
+    _check(lib().amr_load_octree(ctx, n, _buf(level, n, 1, "i", "host", "level"),
+                                 _buf(coord, n * 3, 4, "i", "host", "coord"), _buf(child, n * 8, 4, "i", "host", "child"),
+                                 len(fields), ptrs, int(field_dtype)))
 
 
 def amr_render(ctx, cam: Camera, map_out, count_out=None, out_on_device: int = 1, cuda_stream=None) -> None:

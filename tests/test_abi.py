@@ -93,3 +93,11 @@ def test_binding_checks_buffers_before_the_call():
         amr.amr_blur(None, 16, 16, ok_map, ok_map, 0.1, ok_map)
     with pytest.raises(ValueError, match="elements, need 256"):
         amr.amr_submit(None, cam, torch.zeros(10), None)
+    tree = inputs.plain_tree(np.float64)
+    with pytest.raises(ValueError, match=r"child: .*elements, need"):
+        amr.amr_load_octree(None, tree.n_oct, tree.level, tree.coord, tree.child[:-1], tree.fields, amr.AMR_F64)
+    with pytest.raises(ValueError, match="need float32"):
+        amr.amr_load_octree(None, tree.n_oct, tree.level, tree.coord, tree.child, tree.fields, amr.AMR_F32)
+    with pytest.raises(ValueError, match="need int8"):
+        amr.amr_load_octree(None, tree.n_oct, tree.level.astype(np.int32), tree.coord, tree.child, tree.fields,
+                            amr.AMR_F64)
