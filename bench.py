@@ -178,7 +178,8 @@ def recorded_profile(config):
     if kv.get("kernel_source_sha") != kernel_source_hash():
         return {}
     out = {}
-    for key in ("dram_bytes_per_launch_full_workload", "l1_sector_hit_pct", "l2_sector_hit_pct"):
+    for key in ("dram_bytes_per_launch_full_workload", "l1_sector_hit_pct", "l2_sector_hit_pct", "issue_active_pct",
+                "alu_pipe_pct", "fma_pipe_pct", "thread_inst_per_segment"):
         try:
             out[key] = float(kv[key])
         except (KeyError, ValueError):
@@ -201,6 +202,18 @@ def dram_view(prof, ms, peak):
     gbs = prof["dram_bytes_per_launch_full_workload"] / (ms * 1e-3) / 1e9
     return {"gbs": gbs, "frac": gbs / peak, "l1_sector_hit_pct": prof.get("l1_sector_hit_pct"),
             "l2_sector_hit_pct": prof.get("l2_sector_hit_pct")}
+
+
+def pipe_view(prof):
+    """Issue and pipe utilisation of the committed full capture of this kernel
+    source (what actually bounds it: the integer ALU pipe runs at half the
+    lane rate the essential-ops peak assumes); None without one."""
+    keys = ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct", "thread_inst_per_segment")
+    if not all(k in prof for k in keys):
+        return None
+    out = {k: prof[k] for k in keys}
+    out["source"] = "ncu --set full, first 8 cameras of the batch"
+    return out
 
 
 def max_over_ranks(x: float, device="cpu") -> float:
@@ -513,6 +526,7 @@ def run_ours(args):
         "fp32_vs_fp64_err_per_frame": per_camera if len(cams32) <= 8 else None,
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": alu_achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(args.config),
+                     "pipes": pipe_view(recorded_profile(args.config)),
                      "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz", "ops_per_segment": OPS_PER_SEG,
                      "algorithmic_ops_per_launch": algo_ops,
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -14,6 +14,13 @@ def test_dram_view_from_recorded_profile():
     assert bench.dram_view({}, 100.0, 5000.0) is None
 
 
+def test_pipe_view_needs_every_figure():
+    prof = {"issue_active_pct": 74.0, "alu_pipe_pct": 61.0, "fma_pipe_pct": 22.0, "thread_inst_per_segment": 99.0}
+    v = bench.pipe_view(prof)
+    assert v["alu_pipe_pct"] == 61.0 and "source" in v
+    assert bench.pipe_view({"issue_active_pct": 74.0}) is None
+
+
 def test_recorded_profile_requires_matching_kernel_source(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "batch_kernel_demo_traffic.txt").write_text(
