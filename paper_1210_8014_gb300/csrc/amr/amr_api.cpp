@@ -200,19 +200,29 @@ amr_status grow_st(LaunchSlot& s, int64_t n) {
   return AMR_OK;
 }
 
-// The pixel-centre offsets of one camera, in IEEE double with exactly the
-// operations (and order) of the per-ray formula: s_i = ((i + 0.5) / nx - 0.5)
-// fov0, t_j = ((j + 0.5) / ny - 0.5) fov1.  A row of rays shares t_j and a
-// column s_i, so the kernels read them instead of dividing per ray.
+// The pixel-centre terms of one camera, in IEEE double with exactly the
+// operations (and order) of the per-ray formula x = (centre + s_i u) + t_j v,
+// s_i = ((i + 0.5) / nx - 0.5) fov0, t_j = ((j + 0.5) / ny - 0.5) fov1.  A
+// column of rays shares centre + s_i u and a row t_j v, so the table holds
+// those, already times 2^36 (exact: a power of two), 3 doubles per column then
+// 3 per row; a ray's lattice origin is then rint(A_i + B_j) per axis, the same
+// single rounding of the same two operands as the formula.
 void pixel_offsets(const CamDev& c, double* out) {
-  for (int i = 0; i < c.nx; ++i) out[i] = (((double)i + 0.5) / c.nxd - 0.5) * c.fov0;
-  for (int j = 0; j < c.ny; ++j) out[c.nx + j] = (((double)j + 0.5) / c.nyd - 0.5) * c.fov1;
+  for (int i = 0; i < c.nx; ++i) {
+    const double s = (((double)i + 0.5) / c.nxd - 0.5) * c.fov0;
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = (c.centre[a] + s * c.u[a]) * 68719476736.0;
+  }
+  double* row = out + 3 * (size_t)c.nx;
+  for (int j = 0; j < c.ny; ++j) {
+    const double t = (((double)j + 0.5) / c.nyd - 0.5) * c.fov1;
+    for (int a = 0; a < 3; ++a) row[3 * j + a] = (t * c.v[a]) * 68719476736.0;
+  }
 }
 
 // Fill the slot's offset tables for its first n cameras and point them there.
 amr_status fill_offsets(LaunchSlot& s, int n, int64_t* total) {
   int64_t need = 0;
-  for (int i = 0; i < n; ++i) need += (int64_t)s.h_cams[i].nx + s.h_cams[i].ny;
+  for (int i = 0; i < n; ++i) need += 3 * ((int64_t)s.h_cams[i].nx + s.h_cams[i].ny);
   amr_status st = grow_st(s, need);
   if (st != AMR_OK) return st;
   int64_t o = 0;
@@ -220,7 +230,7 @@ amr_status fill_offsets(LaunchSlot& s, int n, int64_t* total) {
     CamDev& c = s.h_cams[i];
     pixel_offsets(c, s.h_st + o);
     c.st = s.d_st + o;
-    o += (int64_t)c.nx + c.ny;
+    o += 3 * ((int64_t)c.nx + c.ny);
   }
   *total = need;
   return AMR_OK;

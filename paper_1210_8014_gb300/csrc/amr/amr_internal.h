@@ -50,10 +50,11 @@ struct CamDev {
   const void* vel[3];       // wmean velocity fields
   void* map;                // float* or double* [ny][nx]
   int32_t* counts;          // nullable
-  // Pixel-centre offsets, [nx + ny] doubles: s_i = ((i + 0.5) / nx - 0.5) fov0
-  // for i < nx, then t_j likewise with ny and fov1, each rounded exactly as the
-  // per-ray formula would; filled on the host per launch.  Null: the kernels
-  // evaluate the formula per ray.
+  // Pixel-centre terms, [3 (nx + ny)] doubles: (centre + s_i u) 2^36 for each
+  // column i, then (t_j v) 2^36 for each row j (s_i, t_j the pixel offsets along
+  // u and v), each rounded exactly as the per-ray formula rounds it; filled on
+  // the host per launch.  A ray's origin on the 2^-36 lattice is
+  // rint(column term + row term).  Null: the kernels evaluate the formula.
   const double* st;
 };
 

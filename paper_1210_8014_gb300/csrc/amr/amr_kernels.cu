@@ -72,22 +72,27 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   RayOut res{0.0, 0.0f, 0};
 
   // ---- ray set-up: FP64 pixel centre, quantised origin ----------------------
-  // The offsets along u and v come from the launch's per-camera table (the
-  // same IEEE operations, done once per column and row) when there is one.
-  double s, t;
-  if (cam.st) {
-    s = __ldg(cam.st + i);
-    t = __ldg(cam.st + cam.nx + j);
-  } else {
-    s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
-    t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
-  }
+  // With the launch's per-camera table, the column term (centre + s_i u) 2^36
+  // and the row term (t_j v) 2^36 were rounded on the host exactly as below;
+  // one addition and the rounding to the lattice remain per ray.
   long long X[3];
   int D[3], aD[3];
+  if (cam.st) {
+    const double* col = cam.st + 3 * (size_t)i;
+    const double* row = cam.st + 3 * ((size_t)cam.nx + j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) X[a] = __double2ll_rn(__dadd_rn(__ldg(col + a), __ldg(row + a)));
+  } else {
+    const double s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
+    const double t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double x = __dadd_rn(__dadd_rn(cam.centre[a], __dmul_rn(s, cam.u[a])), __dmul_rn(t, cam.v[a]));
+      X[a] = __double2ll_rn(__dmul_rn(x, 68719476736.0 /* 2^36 */));
+    }
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double x = __dadd_rn(__dadd_rn(cam.centre[a], __dmul_rn(s, cam.u[a])), __dmul_rn(t, cam.v[a]));
-    X[a] = __double2ll_rn(__dmul_rn(x, 68719476736.0 /* 2^36 */));
     D[a] = cam.D[a];
     aD[a] = D[a] < 0 ? -D[a] : D[a];
   }

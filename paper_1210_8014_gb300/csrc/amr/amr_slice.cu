@@ -20,22 +20,24 @@ __global__ void __launch_bounds__(256) slice_kernel(const uint2* __restrict__ re
   const int64_t px = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (px >= (int64_t)cam.nx * cam.ny) return;
   const int i = (int)(px % cam.nx), j = (int)(px / cam.nx);
-  double s, t;
-  if (cam.st) {  // per-camera table of the same offsets
-    s = __ldg(cam.st + i);
-    t = __ldg(cam.st + cam.nx + j);
-  } else {
-    s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
-    t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
-  }
   long long X[3];
+  if (cam.st) {  // per-camera column and row terms, rounded as below
+    const double* col = cam.st + 3 * (size_t)i;
+    const double* row = cam.st + 3 * ((size_t)cam.nx + j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) X[a] = __double2ll_rn(__dadd_rn(__ldg(col + a), __ldg(row + a)));
+  } else {
+    const double s = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)i, 0.5), cam.nxd), 0.5), cam.fov0);
+    const double t = __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn((double)j, 0.5), cam.nyd), 0.5), cam.fov1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double x = __dadd_rn(__dadd_rn(cam.centre[a], __dmul_rn(s, cam.u[a])), __dmul_rn(t, cam.v[a]));
+      X[a] = __double2ll_rn(__dmul_rn(x, 68719476736.0 /* 2^36 */));
+    }
+  }
   bool inside = true;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double x = __dadd_rn(__dadd_rn(cam.centre[a], __dmul_rn(s, cam.u[a])), __dmul_rn(t, cam.v[a]));
-    X[a] = __double2ll_rn(__dmul_rn(x, 68719476736.0 /* 2^36 */));
-    inside &= X[a] >= 0 && X[a] < kBoxS;
-  }
+  for (int a = 0; a < 3; ++a) inside &= X[a] >= 0 && X[a] < kBoxS;
   double value = 0.0;
   int level = 0;
   if (inside) {
