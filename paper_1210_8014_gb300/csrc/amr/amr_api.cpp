@@ -56,24 +56,30 @@ struct DeviceTree {
   int64_t bytes = 0;
 };
 
-// One launch's scratch: camera table, tile prefix sums, queue blocks, and the
-// pinned host mirrors they are uploaded from / read back into.
+// One launch's scratch in one device block with a pinned host mirror, laid out
+// per launch so that all a launch uploads is one contiguous prefix: tile
+// prefix sums, queue blocks (zeroed on the host), camera records, pixel-centre
+// tables.  One copy uploads it; the queue blocks come back into the mirror.
 struct LaunchSlot {
-  int cap = 0;  // cameras
-  CamDev* h_cams = nullptr;
+  int cap = 0;                // cameras the tile prefix arrays hold
+  char* h_blob = nullptr;     // pinned host mirror
+  char* d_blob = nullptr;
+  size_t blob_cap = 0;        // bytes of each
+  size_t upload = 0;          // bytes the current layout uploads
+  // Views of the current layout, host and device.
   int32_t* h_tiles = nullptr;  // kMaxPrecisions x (cap + 1)
   QueueBlock* h_q = nullptr;   // kMaxPrecisions
-  CamDev* d_cams = nullptr;
+  CamDev* h_cams = nullptr;
+  double* h_st = nullptr;
   int32_t* d_tiles = nullptr;
   QueueBlock* d_q = nullptr;
+  CamDev* d_cams = nullptr;
+  double* d_st = nullptr;
   cudaEvent_t start = nullptr, done = nullptr;
   bool pending = false;  // a launch whose results are not yet harvested
   int n_groups = 0;
   cudaGraphExec_t gexec = nullptr;  // captured launch sequence of this slot
   std::vector<int64_t> gkey;        // batch shape it was captured for
-  double* h_st = nullptr;           // pixel-centre offset tables, pinned mirror
-  double* d_st = nullptr;
-  int64_t st_cap = 0;               // doubles
 };
 
 struct Request {
@@ -144,59 +150,52 @@ constexpr int kSlots = 8;
 
 void free_slot(LaunchSlot& s) {
   if (s.gexec) cudaGraphExecDestroy(s.gexec);
-  if (s.h_cams) cudaFreeHost(s.h_cams);
-  if (s.h_tiles) cudaFreeHost(s.h_tiles);
-  if (s.h_q) cudaFreeHost(s.h_q);
-  if (s.d_cams) cudaFree(s.d_cams);
-  if (s.d_tiles) cudaFree(s.d_tiles);
-  if (s.d_q) cudaFree(s.d_q);
-  if (s.h_st) cudaFreeHost(s.h_st);
-  if (s.d_st) cudaFree(s.d_st);
+  if (s.h_blob) cudaFreeHost(s.h_blob);
+  if (s.d_blob) cudaFree(s.d_blob);
   s = LaunchSlot{};
 }
 
-amr_status grow_slot(LaunchSlot& s, int n) {
-  if (s.cap >= n && s.h_cams) return AMR_OK;
-  if (s.gexec) cudaGraphExecDestroy(s.gexec);
-  s.gexec = nullptr;
-  s.gkey.clear();
-  int cap = std::max(n, std::max(64, s.cap * 2));
-  if (s.h_cams) cudaFreeHost(s.h_cams);
-  if (s.h_tiles) cudaFreeHost(s.h_tiles);
-  if (s.d_cams) cudaFree(s.d_cams);
-  if (s.d_tiles) cudaFree(s.d_tiles);
-  s.h_cams = nullptr; s.h_tiles = nullptr; s.d_cams = nullptr; s.d_tiles = nullptr;
-  size_t tiles = (size_t)amr::kMaxPrecisions * (cap + 1) * sizeof(int32_t);
-  if (cudaMallocHost((void**)&s.h_cams, cap * sizeof(CamDev)) != cudaSuccess ||
-      cudaMallocHost((void**)&s.h_tiles, tiles) != cudaSuccess ||
-      cudaMalloc((void**)&s.d_cams, cap * sizeof(CamDev)) != cudaSuccess ||
-      cudaMalloc((void**)&s.d_tiles, tiles) != cudaSuccess) {
-    cudaGetLastError();
-    s.cap = 0;
-    return fail(AMR_E_OOM, "cannot allocate launch scratch for %d cameras", n);
+// Lay the slot out for n cameras and st_doubles of pixel-centre tables,
+// growing the block when it is too small (a graph captured against the old
+// block is dropped), and zero the queue blocks in the host mirror.
+amr_status layout_slot(LaunchSlot& s, int n, int64_t st_doubles) {
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const int cap = s.cap >= n ? s.cap : std::max(n, std::max(64, s.cap * 2));
+  const size_t T = up((size_t)amr::kMaxPrecisions * (cap + 1) * sizeof(int32_t));
+  const size_t Q = up(amr::kMaxPrecisions * sizeof(QueueBlock));
+  const size_t C = up((size_t)n * sizeof(CamDev));
+  const size_t total = T + Q + C + (size_t)st_doubles * sizeof(double);
+  if (!s.h_blob || s.blob_cap < total) {
+    if (s.gexec) cudaGraphExecDestroy(s.gexec);
+    s.gexec = nullptr;
+    s.gkey.clear();
+    if (s.h_blob) cudaFreeHost(s.h_blob);
+    if (s.d_blob) cudaFree(s.d_blob);
+    s.h_blob = nullptr;
+    s.d_blob = nullptr;
+    s.blob_cap = 0;
+    const size_t want = std::max(total, std::max<size_t>(size_t(1) << 20, 2 * s.blob_cap));
+    if (cudaMallocHost((void**)&s.h_blob, want) != cudaSuccess || cudaMalloc((void**)&s.d_blob, want) != cudaSuccess) {
+      cudaGetLastError();
+      if (s.h_blob) cudaFreeHost(s.h_blob);
+      s.h_blob = nullptr;
+      s.d_blob = nullptr;
+      s.cap = 0;
+      return fail(AMR_E_OOM, "cannot allocate %zu bytes of launch scratch", want);
+    }
+    s.blob_cap = want;
   }
   s.cap = cap;
-  return AMR_OK;
-}
-
-// Room for n doubles of pixel-centre offset tables in a slot.
-amr_status grow_st(LaunchSlot& s, int64_t n) {
-  if (s.st_cap >= n && s.h_st) return AMR_OK;
-  if (s.gexec) cudaGraphExecDestroy(s.gexec);
-  s.gexec = nullptr;
-  s.gkey.clear();
-  const int64_t cap = std::max<int64_t>(n, std::max<int64_t>(1 << 16, s.st_cap * 2));
-  if (s.h_st) cudaFreeHost(s.h_st);
-  if (s.d_st) cudaFree(s.d_st);
-  s.h_st = nullptr;
-  s.d_st = nullptr;
-  s.st_cap = 0;
-  if (cudaMallocHost((void**)&s.h_st, (size_t)cap * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&s.d_st, (size_t)cap * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(AMR_E_OOM, "cannot allocate %lld pixel offsets", (long long)n);
-  }
-  s.st_cap = cap;
+  s.upload = total;
+  s.h_tiles = (int32_t*)s.h_blob;
+  s.d_tiles = (int32_t*)s.d_blob;
+  s.h_q = (QueueBlock*)(s.h_blob + T);
+  s.d_q = (QueueBlock*)(s.d_blob + T);
+  s.h_cams = (CamDev*)(s.h_blob + T + Q);
+  s.d_cams = (CamDev*)(s.d_blob + T + Q);
+  s.h_st = (double*)(s.h_blob + T + Q + C);
+  s.d_st = (double*)(s.d_blob + T + Q + C);
+  std::memset(s.h_q, 0, Q);
   return AMR_OK;
 }
 
@@ -219,32 +218,27 @@ void pixel_offsets(const CamDev& c, double* out) {
   }
 }
 
-// Fill the slot's offset tables for its first n cameras and point them there.
-amr_status fill_offsets(LaunchSlot& s, int n, int64_t* total) {
-  int64_t need = 0;
-  for (int i = 0; i < n; ++i) need += 3 * ((int64_t)s.h_cams[i].nx + s.h_cams[i].ny);
-  amr_status st = grow_st(s, need);
-  if (st != AMR_OK) return st;
+// Doubles of pixel-centre tables a camera needs.
+int64_t offset_doubles(const CamDev& c) { return 3 * ((int64_t)c.nx + c.ny); }
+
+// Fill the slot's pixel-centre tables for its first n cameras (laid out for
+// them) and point the camera records there.
+void fill_offsets(LaunchSlot& s, int n) {
   int64_t o = 0;
   for (int i = 0; i < n; ++i) {
     CamDev& c = s.h_cams[i];
     pixel_offsets(c, s.h_st + o);
     c.st = s.d_st + o;
-    o += 3 * ((int64_t)c.nx + c.ny);
+    o += offset_doubles(c);
   }
-  *total = need;
-  return AMR_OK;
 }
 
 amr_status init_slots(amr_ctx* ctx) {
   ctx->slots.resize(kSlots);
   for (auto& s : ctx->slots) {
-    CUDA_TRY(cudaMallocHost((void**)&s.h_q, amr::kMaxPrecisions * sizeof(QueueBlock)));
-    CUDA_TRY(cudaMalloc((void**)&s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock)));
     CUDA_TRY(cudaEventCreate(&s.start));
     CUDA_TRY(cudaEventCreate(&s.done));
-    std::memset(s.h_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock));
-    amr_status st = grow_slot(s, 64);
+    amr_status st = layout_slot(s, 64, 0);
     if (st != AMR_OK) return st;
   }
   return AMR_OK;
@@ -442,7 +436,9 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     harvest(ctx, s);
   }
   const int n = (int)cams.size();
-  amr_status st = grow_slot(s, n);
+  int64_t st_total = 0;
+  for (const CamDev& c : cams) st_total += offset_doubles(c);
+  amr_status st = layout_slot(s, n, st_total);
   if (st != AMR_OK) return st;
   // Order cameras by precision group; each group gets its own prefix table.
   int groups[amr::kMaxPrecisions] = {0, 0, 0};
@@ -451,9 +447,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   for (int g = 0; g < amr::kMaxPrecisions; ++g) gstart[g + 1] = gstart[g] + groups[g];
   int fill[amr::kMaxPrecisions] = {gstart[0], gstart[1], gstart[2]};
   for (int i = 0; i < n; ++i) s.h_cams[fill[precs[i]]++] = cams[i];
-  int64_t st_total = 0;
-  st = fill_offsets(s, n, &st_total);
-  if (st != AMR_OK) return st;
+  fill_offsets(s, n);
   int64_t tiles_total[amr::kMaxPrecisions] = {0, 0, 0};
   for (int g = 0; g < amr::kMaxPrecisions; ++g) {
     int32_t* tp = s.h_tiles + (size_t)g * (s.cap + 1);
@@ -495,17 +489,13 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     const int64_t blocks_needed = (warps_needed * 32 + opt.block_threads - 1) / opt.block_threads;
     grids[g] = (int)std::max<int64_t>(1, std::min(grid, blocks_needed));
   }
-  const size_t tile_bytes = (size_t)amr::kMaxPrecisions * (s.cap + 1) * sizeof(int32_t);
   // In a capture the two events must become event-record nodes of the graph
   // (external records), not capture-internal dependencies.
   auto record = [&](cudaStream_t st, bool capturing) -> cudaError_t {
     const unsigned ev = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     cudaError_t e = cudaEventRecordWithFlags(s.start, st, ev);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_cams, s.h_cams, n * sizeof(CamDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_tiles, s.h_tiles, tile_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(s.d_st, s.h_st, (size_t)st_total * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), st);
+    // one upload: tile prefix sums, zeroed queue blocks, cameras, pixel tables
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_blob, s.h_blob, s.upload, cudaMemcpyHostToDevice, st);
     for (int g = 0; g < amr::kMaxPrecisions && e == cudaSuccess; ++g)
       if (grids[g]) e = amr::launch_batch(g, ctx->tree.f64, args[g], grids[g], opt.block_threads, st);
     if (e == cudaSuccess)
@@ -554,7 +544,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   s.pending = true;
   ctx->n_renders++;
   ctx->n_cams += n;
-  ctx->n_h2d_bytes += (int64_t)(n * sizeof(CamDev) + tile_bytes) + st_total * (int64_t)sizeof(double);
+  ctx->n_h2d_bytes += (int64_t)s.upload;
   for (const CamDev& c : cams) ctx->n_rays += (int64_t)c.nx * c.ny;
   if (used) *used = &s;
   return AMR_OK;
@@ -570,16 +560,14 @@ amr_status enqueue_slice(amr_ctx* ctx, const CamDev& cam, bool out64, cudaStream
     CUDA_TRY(cudaEventSynchronize(s.done));
     harvest(ctx, s);
   }
-  s.h_cams[0] = cam;
-  int64_t st_total = 0;
-  amr_status st = fill_offsets(s, 1, &st_total);
+  amr_status st = layout_slot(s, 1, offset_doubles(cam));
   if (st != AMR_OK) return st;
+  s.h_cams[0] = cam;
+  fill_offsets(s, 1);
   s.n_groups = amr::kMaxPrecisions;
   CUDA_TRY(cudaEventRecord(s.start, stream));
-  CUDA_TRY(cudaMemcpyAsync(s.d_cams, s.h_cams, sizeof(CamDev), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemcpyAsync(s.d_st, s.h_st, (size_t)st_total * sizeof(double), cudaMemcpyHostToDevice, stream));
-  ctx->n_h2d_bytes += (int64_t)sizeof(CamDev) + st_total * (int64_t)sizeof(double);
-  CUDA_TRY(cudaMemsetAsync(s.d_q, 0, amr::kMaxPrecisions * sizeof(QueueBlock), stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_blob, s.h_blob, s.upload, cudaMemcpyHostToDevice, stream));
+  ctx->n_h2d_bytes += (int64_t)s.upload;
   CUDA_TRY(amr::launch_slice(out64, ctx->tree.f64, ctx->tree.rec, (uint32_t)ctx->tree.n_oct, s.d_cams,
                              (int64_t)cam.nx * cam.ny, &s.d_q[0].error, stream));
   CUDA_TRY(cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, stream));
