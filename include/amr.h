@@ -113,10 +113,11 @@ amr_status amr_destroy(amr_ctx* ctx);
  * coord 0; child level = parent level + 1; child coord = 2 (parent coord + offset
  * of c); every non-root oct referenced exactly once; coordinates in range.
  * The arrays are renumbered breadth-first (siblings contiguous) into 8-byte oct
- * records {first child, refinement mask | level << 8}, 32-byte link blocks (six
- * face links and the packed oct coordinates) and one array per field, and copied
- * to device memory owned by the context (40 B + 8 x field size per oct); the
- * caller may free its arrays on return.
+ * records {first child, refinement mask | level << 8}, 64-byte link blocks (six
+ * face links, each with the linked oct's mask and level, and the packed oct
+ * coordinates) and one array per field, and copied to device memory owned by
+ * the context (72 B + 8 x field size per oct); the caller may free its arrays
+ * on return.
  * Synchronous.
  */
 amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, const int32_t* coord,
@@ -233,13 +234,64 @@ amr_status amr_cancel(amr_ctx* ctx, uint64_t ticket);
  * call before any stream capture.  All calls share the scratch and clear its
  * queue at the start: calls that overlap on the GPU race on it, so order them
  * on one stream.  Record contents are not validated on the host; a child index
- * at or beyond n_oct ends that ray instead of being read.
+ * at or beyond n_oct ends that ray instead of being read, and the kernel records
+ * it (and a ray that reaches the step cap) in the scratch's error word, which
+ * amr_noalloc_status reports; the call itself has already returned AMR_OK.
+ * The scratch's device address is looked up once per device ordinal and kept
+ * for the life of the process: do not use this entry point across a
+ * cudaDeviceReset or from a CUDA context other than the device's primary one.
  */
 #define AMR_NOALLOC_MAX_CAMERAS 256
 amr_status amr_render_batch_noalloc(int64_t n_oct, const uint64_t* records, int32_t depth, int32_t n_fields,
                                     const void* const* fields, int32_t field_dtype, int32_t n,
                                     const amr_camera* cams, void* const* maps, int32_t* const* counts,
                                     void* cuda_stream);
+
+/*
+ * Device status of the last amr_render_batch_noalloc on the calling thread's
+ * current device (the paper has no counterpart).  Synchronises cuda_stream
+ * (pass the stream the batch ran on), then writes into caller host memory
+ * (each pointer nullable): *host_error 0 (no error), 1 (a child index at or
+ * beyond n_oct ended a ray; *host_oct is the oct that held it) or 2 (a ray hit
+ * the step cap of 2^25 leaves, which only a corrupted tree reaches);
+ * *host_segments the leaves crossed over all rays.  Allocates nothing.
+ * AMR_E_INVALID if no no-allocation batch has run on this device.
+ */
+amr_status amr_noalloc_status(void* cuda_stream, int32_t* host_error, int32_t* host_oct, uint64_t* host_segments);
+
+/*
+ * Sort-last rendering (Sec. 3.1: the data is split among processes, each
+ * renders its own part, and the partial images are merged; Sec. 2.2: the
+ * leaves' contributions are added in any order, so partial sums over disjoint
+ * leaf domains add up to the whole ray's sum).
+ *
+ * amr_render_batch_partial renders like amr_render_batch with device outputs,
+ * but stores each pixel's accumulators instead of the finished value, so that
+ * renders of disjoint leaf domains (trees whose cells outside the domain hold
+ * zero density) can be merged exactly.  partials[i]: device memory, nx*ny
+ * elements of
+ *                     FP32 precisions                      AMR_PREC_FP64
+ *   column            float2 (high, low), value = high+low  double
+ *   wmean, level      float4 (S high, S low, N high, N low)  double2 (S, N)
+ *   max               float                                  double
+ * where S = sum rho*len and N the weighted numerator (sum rho*(v.w)*len, or
+ * sum rho*len*level).  counts as in amr_render_batch (per domain: they include
+ * the zero-valued cells the domain's tree holds).
+ *
+ * amr_merge_partials merges n_parts partial maps of one camera (same mode and
+ * precision) into the finished map (device, nx*ny floats, or doubles for
+ * AMR_PREC_FP64): sums are added with error-free TwoSum transformations and
+ * their errors carried in a second accumulator, the weighted mean is N / S
+ * (0 where S = 0), and max takes the largest value.  1 <= n_parts <=
+ * AMR_MERGE_MAX_PARTS; n_px = nx*ny.  partials is a host array of device
+ * pointers.  Runs on the calling thread's current device, enqueued on
+ * cuda_stream; allocates nothing.
+ */
+#define AMR_MERGE_MAX_PARTS 64
+amr_status amr_render_batch_partial(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* partials,
+                                    int32_t* const* counts, void* cuda_stream);
+amr_status amr_merge_partials(int32_t n_parts, int32_t mode, int32_t precision, int64_t n_px,
+                              const void* const* partials, void* map_out, void* cuda_stream);
 
 /* JSON counters: renders, rays, segments, tree bytes, options, server latency. */
 amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len);

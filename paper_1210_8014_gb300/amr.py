@@ -83,6 +83,9 @@ def lib():
             "amr_tree_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)],
             "amr_render_batch_noalloc": [I64, P, I32, I32, ctypes.POINTER(P), I32, I32, ctypes.POINTER(amr_camera),
                                          ctypes.POINTER(P), ctypes.POINTER(P), P],
+            "amr_noalloc_status": [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_uint64)],
+            "amr_render_batch_partial": [P, I32, ctypes.POINTER(amr_camera), ctypes.POINTER(P), ctypes.POINTER(P), P],
+            "amr_merge_partials": [I32, I32, I32, I64, ctypes.POINTER(P), P, P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -142,6 +145,13 @@ def _buf(x, n: int, itemsize: int, kind: str, where: Optional[str], name: str) -
         raise ValueError(f"{name}: {count} elements, need {n}")
     if where == "device" and not dev:
         raise ValueError(f"{name}: a host buffer where a device buffer is needed")
+    if where == "current-device":
+        import torch
+        if not dev:
+            raise ValueError(f"{name}: a host buffer where a device buffer is needed")
+        if x.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name}: on cuda:{x.device.index}, but the call runs on the current device "
+                             f"cuda:{torch.cuda.current_device()}")
     if where == "host" and dev:
         raise ValueError(f"{name}: a device buffer where a host buffer is needed")
     return ptr()
@@ -300,16 +310,65 @@ def amr_render_batch_noalloc(n_oct: int, records, depth: int, fields: Sequence, 
     """Batch render with no GPU allocation: tree, maps and counts are the caller's device buffers."""
     n = len(cams)
     fsize = 8 if int(field_dtype) == AMR_F64 else 4
-    farr = (ctypes.c_void_p * len(fields))(*[_buf(f, int(n_oct) * 8, fsize, "f", "device", f"fields[{i}]")
+    farr = (ctypes.c_void_p * len(fields))(*[_buf(f, int(n_oct) * 8, fsize, "f", "current-device", f"fields[{i}]")
                                              for i, f in enumerate(fields)])
     carr = (amr_camera * max(n, 1))(*[to_camera(c) for c in cams])
-    marr = (ctypes.c_void_p * max(n, 1))(*[_buf(m, int(c.nx) * int(c.ny), _map_size(c), "f", "device", f"maps[{i}]")
+    marr = (ctypes.c_void_p * max(n, 1))(*[_buf(m, int(c.nx) * int(c.ny), _map_size(c), "f", "current-device", f"maps[{i}]")
                                            for i, (m, c) in enumerate(zip(maps, cams))])
-    karr = (ctypes.c_void_p * max(n, 1))(*[_buf(k, int(c.nx) * int(c.ny), 4, "i", "device", f"counts[{i}]")
+    karr = (ctypes.c_void_p * max(n, 1))(*[_buf(k, int(c.nx) * int(c.ny), 4, "i", "current-device", f"counts[{i}]")
                                            for i, (k, c) in enumerate(zip(counts, cams))]) if counts is not None else None
-    recs = _buf(records, int(n_oct), 8, "i", "device", "records")
+    recs = _buf(records, int(n_oct), 8, "i", "current-device", "records")
     _check(lib().amr_render_batch_noalloc(int(n_oct), recs, int(depth), len(fields), farr, int(field_dtype),
                                           n, carr, marr, karr, _ptr(cuda_stream) if cuda_stream is not None else None))
+
+
+def amr_noalloc_status(cuda_stream=None) -> dict:
+    """Device status of the last no-allocation batch on the current device
+    (synchronises the stream): error 0 ok, 1 bad child index (oct), 2 step cap."""
+    err, oct_, segs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+    _check(lib().amr_noalloc_status(_ptr(cuda_stream) if cuda_stream is not None else None, ctypes.byref(err),
+                                    ctypes.byref(oct_), ctypes.byref(segs)))
+    return {"error": int(err.value), "oct": int(oct_.value), "segments": int(segs.value)}
+
+
+AMR_MERGE_MAX_PARTS = 64
+
+
+def partial_components(mode: int, precision: int) -> int:
+    """Values per pixel of a partial render: FP32 column (high, low) 2, weighted
+    (S high, S low, N high, N low) 4, max 1; FP64 column 1, weighted (S, N) 2,
+    max 1 (float32 or float64 elements)."""
+    weighted = int(mode) in (AMR_MODE_WMEAN, AMR_MODE_LEVEL)
+    if int(precision) == AMR_PREC_FP64:
+        return 2 if weighted else 1
+    return 4 if weighted else (1 if int(mode) == AMR_MODE_MAX else 2)
+
+
+def amr_render_batch_partial(ctx, cams: Sequence[Camera], partials: Sequence, counts: Optional[Sequence] = None,
+                             cuda_stream=None) -> None:
+    """Sort-last partial renders (device buffers): each pixel's accumulators."""
+    n = len(cams)
+    if len(partials) != n or (counts is not None and len(counts) != n):
+        raise ValueError("one partial (and one counts entry, if counts are given) per camera")
+    carr = (amr_camera * n)(*[to_camera(c) for c in cams])
+    parr = (ctypes.c_void_p * n)(*[_buf(m, int(c.nx) * int(c.ny) * partial_components(c.mode, c.precision),
+                                        _map_size(c), "f", "device", f"partials[{i}]")
+                                   for i, (m, c) in enumerate(zip(partials, cams))])
+    karr = (ctypes.c_void_p * n)(*[_buf(k, int(c.nx) * int(c.ny), 4, "i", "device", f"counts[{i}]")
+                                   for i, (k, c) in enumerate(zip(counts, cams))]) if counts is not None else None
+    _check(lib().amr_render_batch_partial(ctx, n, carr, parr, karr,
+                                          _ptr(cuda_stream) if cuda_stream is not None else None))
+
+
+def amr_merge_partials(mode: int, precision: int, n_px: int, partials: Sequence, map_out, cuda_stream=None) -> None:
+    """Merge partial renders of one camera into its map (device buffers)."""
+    size = 8 if int(precision) == AMR_PREC_FP64 else 4
+    comps = partial_components(mode, precision)
+    parr = (ctypes.c_void_p * max(len(partials), 1))(*[_buf(q, int(n_px) * comps, size, "f", "current-device",
+                                                            f"partials[{i}]") for i, q in enumerate(partials)])
+    m = _buf(map_out, int(n_px), size, "f", "current-device", "map_out")
+    _check(lib().amr_merge_partials(len(partials), int(mode), int(precision), int(n_px), parr, m,
+                                    _ptr(cuda_stream) if cuda_stream is not None else None))
 
 
 # ---------------------------------------------------------------- convenience
@@ -356,6 +415,20 @@ class Renderer:
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
         amr_render_batch(self.ctx, cams, [o[0] for o in outs], [o[1] for o in outs] if with_counts else None, 1,
                          s.cuda_stream)
+        return outs
+
+    def alloc_partial(self, cam: Camera):
+        t = self.torch
+        dt = t.float64 if cam.precision == AMR_PREC_FP64 else t.float32
+        dev = f"cuda:{self.device}"
+        k = partial_components(cam.mode, cam.precision)
+        return t.empty((cam.ny, cam.nx, k), dtype=dt, device=dev), t.empty((cam.ny, cam.nx), dtype=t.int32, device=dev)
+
+    def render_partial(self, cams: Sequence[Camera], stream=None):
+        """Partial renders (sort-last domain shares) of cams: [(partial, counts)]."""
+        outs = [self.alloc_partial(c) for c in cams]
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        amr_render_batch_partial(self.ctx, cams, [o[0] for o in outs], [o[1] for o in outs], s.cuda_stream)
         return outs
 
     def slice(self, cam: Camera, stream=None):

@@ -48,7 +48,7 @@ amr_status fail(amr_status st, const char* fmt, ...) {
 
 struct DeviceTree {
   uint2* rec = nullptr;
-  int32_t* nbr = nullptr;  // [n_oct][8] link blocks: six face links + packed coordinates
+  int2* nbr = nullptr;  // [n_oct][8] 64-byte link blocks: six face links + packed coordinates
   std::vector<void*> fields;
   int64_t n_oct = 0;
   int depth = 0;
@@ -427,7 +427,7 @@ amr_status check_options(const amr_options& o) {
 // Enqueue one batch of canonical cameras (map/count pointers already device
 // pointers) on `stream`: one persistent launch per precision present.
 amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDev>& cams,
-                   const std::vector<int>& precs, cudaStream_t stream, LaunchSlot** used) {
+                   const std::vector<int>& precs, cudaStream_t stream, LaunchSlot** used, bool partial = false) {
   std::unique_lock<std::mutex> lk(ctx->launch_mu);
   LaunchSlot& s = ctx->slots[ctx->next_slot];
   ctx->next_slot = (ctx->next_slot + 1) % ctx->slots.size();
@@ -477,6 +477,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     a.tile_w = opt.tile_w;
     a.tile_h = opt.tile_h;
     a.tiles_per_grab = opt.tiles_per_grab;
+    a.partial = partial ? 1 : 0;
     a.q = s.d_q + g;
     int bps = opt.blocks_per_sm;
     if (bps <= 0) {
@@ -507,7 +508,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   if (opt.use_graph) {
     // Replay a captured graph of this slot when the batch shape is unchanged
     // (the camera table itself is read from the slot's pinned staging).
-    std::vector<int64_t> key = {n, s.cap, (int64_t)(uintptr_t)s.d_cams, st_total, (int64_t)(uintptr_t)s.d_st,
+    std::vector<int64_t> key = {n, partial ? 1 : 0, s.cap, (int64_t)(uintptr_t)s.d_cams, st_total, (int64_t)(uintptr_t)s.d_st,
                                 (int64_t)(uintptr_t)ctx->tree.rec,
                                 (int64_t)(uintptr_t)ctx->tree.nbr, ctx->tree.f64, opt.block_threads,
                                 opt.tile_w, opt.tile_h, opt.tiles_per_grab};
@@ -612,7 +613,7 @@ void* host_alias(void* p) {
 }
 
 amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps, int32_t* const* counts,
-                       int out_on_device, void* cuda_stream) {
+                       int out_on_device, void* cuda_stream, bool partial = false) {
   if (!ctx) return fail(AMR_E_INVALID, "null context");
   if (n < 0 || (n > 0 && (!cams || !maps))) return fail(AMR_E_INVALID, "bad batch arguments");
   if (n == 0) return AMR_OK;
@@ -633,7 +634,7 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
       dev[i].counts = counts ? counts[i] : nullptr;
     }
     LaunchSlot* s = nullptr;
-    return enqueue(ctx, opt, dev, precs, stream, &s);
+    return enqueue(ctx, opt, dev, precs, stream, &s, partial);
   }
   // Host outputs: a camera whose map (and counts) the GPU can address is
   // written in place; the others go to device staging and are copied back.
@@ -1017,14 +1018,22 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
   std::vector<int32_t> nb;
   try {
     build_neighbours(rec, nb);
-    // One 32-byte block per oct: its six links, then its corner coordinates
-    // (even, < 2^22) halved and packed into 64 bits.
-    std::vector<int32_t> blocks((size_t)n_oct * 8);
+    // One 64-byte block per oct: its six links as 8-byte words {link, the
+    // linked oct's refinement mask | level << 8} (0 beside -1), then its corner
+    // coordinates (even, < 2^22) halved and packed into 64 bits, then unused.
+    std::vector<int32_t> blocks((size_t)n_oct * 16, 0);
     for (int64_t p = 0; p < n_oct; ++p) {
-      for (int q = 0; q < 6; ++q) blocks[(size_t)p * 8 + q] = nb[(size_t)p * 6 + q];
+      for (int q = 0; q < 6; ++q) {
+        const int32_t v = nb[(size_t)p * 6 + q];
+        blocks[(size_t)p * 16 + 2 * q] = v;
+        uint32_t ry = 0;
+        if (v >= 0) ry = rec[v].y;
+        else if (v <= -2) ry = rec[(uint32_t)(-v - 2) >> 3].y;
+        blocks[(size_t)p * 16 + 2 * q + 1] = (int32_t)ry;
+      }
       const int32_t* cc = coord + (size_t)order[p] * 3;
       const uint64_t pk = (uint64_t)(cc[0] >> 1) | ((uint64_t)(cc[1] >> 1) << 21) | ((uint64_t)(cc[2] >> 1) << 42);
-      std::memcpy(&blocks[(size_t)p * 8 + 6], &pk, sizeof pk);
+      std::memcpy(&blocks[(size_t)p * 16 + 12], &pk, sizeof pk);
     }
     nb.swap(blocks);
   } catch (const std::bad_alloc&) {
@@ -1055,13 +1064,13 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
       return fail(AMR_E_OOM, "device memory for field %d (%zu bytes)", f, fbytes);
     }
   }
-  if (cudaMalloc((void**)&t.nbr, (size_t)n_oct * 8 * sizeof(int32_t)) != cudaSuccess) {
+  if (cudaMalloc((void**)&t.nbr, (size_t)n_oct * 16 * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
     free_tree(t);
     return fail(AMR_E_OOM, "device memory for %lld neighbour link blocks", (long long)n_oct);
   }
   cudaError_t e = cudaMemcpy(t.rec, rec.data(), (size_t)n_oct * sizeof(uint2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(t.nbr, nb.data(), (size_t)n_oct * 8 * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(t.nbr, nb.data(), (size_t)n_oct * 16 * sizeof(int32_t), cudaMemcpyHostToDevice);
   std::vector<char> buf;
   try {
     buf.resize(fbytes);
@@ -1081,7 +1090,7 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
   t.n_oct = n_oct;
   t.depth = depth;
   t.f64 = field_dtype == AMR_F64;
-  t.bytes = (int64_t)(n_oct * (sizeof(uint2) + 8 * sizeof(int32_t)) + n_fields * fbytes);
+  t.bytes = (int64_t)(n_oct * (sizeof(uint2) + 16 * sizeof(int32_t)) + n_fields * fbytes);
   ctx->tree = std::move(t);
   return AMR_OK;
 }
@@ -1097,6 +1106,11 @@ amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_
 amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
                             int32_t* const* counts, int out_on_device, void* cuda_stream) {
   return render_impl(ctx, n, cams, maps, counts, out_on_device, cuda_stream);
+}
+
+amr_status amr_render_batch_partial(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* partials,
+                                    int32_t* const* counts, void* cuda_stream) {
+  return render_impl(ctx, n, cams, partials, counts, 1, cuda_stream, true);
 }
 
 amr_status amr_slice(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_t* level_out, int out_on_device,

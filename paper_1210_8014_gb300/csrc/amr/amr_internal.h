@@ -69,16 +69,18 @@ struct QueueBlock {
 
 struct BatchArgs {
   const uint2* rec;         // oct records {first child, refinement mask | level << 8}
-  const int32_t* nbr;       // [n_oct][8]: six face-neighbour links, then the oct's
-                            // corner coordinates halved, packed x | y << 21 | z << 42
-                            // in 64 bits; or null (then the
-                            // kernel finds neighbours through its ancestor stack)
+  const int2* nbr;          // [n_oct][8]: six face-neighbour links {target, the
+                            // target oct's mask | level << 8}, then the oct's corner
+                            // coordinates halved, packed x | y << 21 | z << 42; or
+                            // null (then the kernel finds neighbours through its
+                            // ancestor stack)
   uint32_t n_oct;
   int32_t n_cams;
   const CamDev* cams;
   const int32_t* tile_start;  // [n_cams + 1] prefix sums of tiles
   int32_t total_tiles;
   int32_t tile_w, tile_h, tiles_per_grab;
+  int32_t partial;            // 1: store each pixel's accumulators (a sort-last partial)
   QueueBlock* q;
 };
 

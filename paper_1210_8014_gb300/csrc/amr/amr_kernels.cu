@@ -26,7 +26,9 @@
 //
 // Oct records are 8 bytes {index of the first child oct, 8-bit refinement
 // mask | level << 8}; siblings are contiguous, so the child of cell c is
-// first + popc(mask & ((1 << c) - 1)).  Field values are one array per field,
+// first + popc(mask & ((1 << c) - 1)).  Each oct also has a 64-byte link block:
+// six 8-byte face links {neighbour, the neighbour oct's mask | level << 8} and
+// the oct's packed corner coordinates.  Field values are one array per field,
 // indexed oct * 8 + cell.
 #include "amr_internal.h"
 #include "amr.h"
@@ -61,15 +63,17 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
   s = t;
 }
 
+// A ray's accumulators: FP64 sums (s = column / denominator, n = weighted
+// numerator, m = maximum), or FP32 ones with their compensation terms.
 struct RayOut {
-  double d;
-  float f;
+  double s, n, m;
+  float sf, cs, nf, cn, mf;
   int count;
 };
 
 template <int PREC, int MODE, bool NB, typename F>
 __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& cam, int i, int j) {
-  RayOut res{0.0, 0.0f, 0};
+  RayOut res{0.0, 0.0, 0.0, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0};
 
   // ---- ray set-up: FP64 pixel centre, quantised origin ----------------------
   // With the launch's per-camera table, the column term (centre + s_i u) 2^36
@@ -165,8 +169,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       }
       c = (k0 & 1) | ((k1 & 1) << 1) | ((k2 & 1) << 2);
       if (!((r.y >> c) & 1u) || q >= L) break;
-      o = r.x + __popc(r.y & ((1u << c) - 1u));
-      if (o >= A.n_oct) { bad = true; break; }
+      const uint32_t ch = r.x + __popc(r.y & ((1u << c) - 1u));
+      if (ch >= A.n_oct) { bad = true; break; }  // o still names the oct holding the bad index
+      o = ch;
       ++q;
       if (!NB) stack[q] = o;
       r = __ldg(&rec[o]);
@@ -314,22 +319,29 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         c ^= stepbits;
         // One axis leaves the oct: its face link (the slot comes with the
         // increments) is the same-level oct there, the coarser leaf covering
-        // that side, or -1 where the box ends.  The common case (a same-level
-        // oct) runs as predicated loads, no branch.
+        // that side, or -1 where the box ends.  The link carries the target
+        // oct's refinement mask and level, so a same-level step reads one
+        // 8-byte word (no dependent record load); the first-child index is
+        // read only when the ray descends.
         int v = (int)o;
-        if (!inoct) v = __ldg(&A.nbr[o * 8u + (uint32_t)(dF.w & 7)]);
+        uint32_t ry = r.y;
+        if (!inoct) {
+          const int2 lk = __ldg(&A.nbr[o * 8u + (uint32_t)(dF.w & 7)]);
+          v = lk.x;
+          ry = (uint32_t)lk.y;
+        }
         if (v >= 0) {
           if ((uint32_t)v >= A.n_oct) { bad = true; break; }
-          if (!inoct) r = __ldg(&rec[v]);
+          r.y = ry;
           o = (uint32_t)v;
         } else {
           if (v == -1) break;
           // A coarser leaf: an unrefined cell, so the test below skips it.
           const int cr = -v - 2;
+          if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
           o = (uint32_t)cr >> 3;
-          if (o >= A.n_oct) { bad = true; break; }
           c = cr & 7;
-          r = __ldg(&rec[o]);
+          r.y = ry;
           lvl = (int)((r.y >> 8) & 31u);
           if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
           load_k();
@@ -343,8 +355,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           const long long Xa = sel3(ea, X[0], X[1], X[2]);
           m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
           dA = sel3(ea, aD[0], aD[1], aD[2]);
-          o = r.x + __popc(r.y & ((1u << c) - 1u));
-          if (o >= A.n_oct) { bad = true; break; }
+          const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+          if (ch >= A.n_oct) { bad = true; break; }
+          o = ch;
           r = __ldg(&rec[o]);
           descend(lvl + 1, lvl, k0, k1, k2);
           if (bad) break;
@@ -386,8 +399,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           const long long Xa = sel3(ea, X[0], X[1], X[2]);
           m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
           dA = sel3(ea, aD[0], aD[1], aD[2]);
-          o = r.x + __popc(r.y & ((1u << c) - 1u));
-          if (o >= A.n_oct) { bad = true; break; }
+          const uint32_t ch = r.x + __popc(r.y & ((1u << c) - 1u));
+          if (ch >= A.n_oct) { bad = true; break; }
+          o = ch;
           stack[lvl + 1] = o;
           r = __ldg(&rec[o]);
           descend(lvl + 1, lvl, j0, j1, j2);
@@ -411,50 +425,74 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     }
   }
   if (count >= kStepCap) atomicExch(&A.q->error, (int)kDevStepCap);
-  if (bad) {
+  if (bad) {  // o: the oct whose record or link held the bad index
     atomicExch(&A.q->error, (int)kDevBadOct);
     atomicExch(&A.q->err_oct, (int)o);
   }
 
   res.count = count;
-  if (PREC == AMR_PREC_FP64) {
-    if (MODE == AMR_MODE_COLUMN) res.d = Sd;
-    else if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) res.d = Sd != 0.0 ? Nd / Sd : 0.0;
-    else res.d = Md;
-  } else {
-    if (MODE == AMR_MODE_COLUMN) {
-      res.f = PREC == AMR_PREC_FP32_KAHAN ? __fsub_rn(Sf, cSf) : Sf;
-    } else if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) {
-      const float S = PREC == AMR_PREC_FP32_KAHAN ? __fsub_rn(Sf, cSf) : Sf;
-      const float N = PREC == AMR_PREC_FP32_KAHAN ? __fadd_rn(Nf, cNf) : Nf;
-      res.f = S != 0.0f ? __fdiv_rn(N, S) : 0.0f;
-    } else {
-      res.f = Mf;
-    }
-  }
+  res.s = Sd; res.n = Nd; res.m = Md;
+  // Compensated FP32 sums as (high, low) pairs whose sum is the value: Kahan's
+  // term is subtracted (s - c), Neumaier's added (n + c).
+  res.sf = Sf; res.cs = PREC == AMR_PREC_FP32_KAHAN ? -cSf : 0.0f;
+  res.nf = Nf; res.cn = PREC == AMR_PREC_FP32_KAHAN ? cNf : 0.0f;
+  res.mf = Mf;
   return res;
 }
 
-template <int PREC, bool NB, typename F>
-__device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& cam, int i, int j) {
-  RayOut o;
-  switch (cam.mode) {
-    case AMR_MODE_COLUMN: o = trace_ray<PREC, AMR_MODE_COLUMN, NB, F>(A, cam, i, j); break;
-    case AMR_MODE_WMEAN: o = trace_ray<PREC, AMR_MODE_WMEAN, NB, F>(A, cam, i, j); break;
-    case AMR_MODE_LEVEL: o = trace_ray<PREC, AMR_MODE_LEVEL, NB, F>(A, cam, i, j); break;
-    default: o = trace_ray<PREC, AMR_MODE_MAX, NB, F>(A, cam, i, j); break;
+// Finalise a ray (wmean = N / S, 0 on an empty ray) and store it, or, for a
+// partial render (a sort-last domain's share, Sec. 3.1), store the
+// accumulators themselves so that domains can be merged later.
+template <int PREC, int MODE, bool PARTIAL>
+__device__ __forceinline__ void store_pixel(const CamDev& cam, size_t px, const RayOut& o) {
+  constexpr bool weighted = MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL;
+  if (PARTIAL) {
+    if (PREC == AMR_PREC_FP64) {
+      if (weighted) static_cast<double2*>(cam.map)[px] = make_double2(o.s, o.n);
+      else static_cast<double*>(cam.map)[px] = MODE == AMR_MODE_MAX ? o.m : o.s;
+    } else {
+      if (weighted) static_cast<float4*>(cam.map)[px] = make_float4(o.sf, o.cs, o.nf, o.cn);
+      else if (MODE == AMR_MODE_MAX) static_cast<float*>(cam.map)[px] = o.mf;
+      else static_cast<float2*>(cam.map)[px] = make_float2(o.sf, o.cs);
+    }
+  } else if (PREC == AMR_PREC_FP64) {
+    double v = MODE == AMR_MODE_MAX ? o.m : o.s;
+    if (weighted) v = o.s != 0.0 ? o.n / o.s : 0.0;
+    static_cast<double*>(cam.map)[px] = v;
+  } else {
+    float v = o.mf;
+    if (MODE != AMR_MODE_MAX) {
+      const float S = __fadd_rn(o.sf, o.cs);
+      v = S;
+      if (weighted) v = S != 0.0f ? __fdiv_rn(__fadd_rn(o.nf, o.cn), S) : 0.0f;
+    }
+    static_cast<float*>(cam.map)[px] = v;
   }
+}
+
+template <int PREC, int MODE, bool NB, typename F, bool PARTIAL>
+__device__ __forceinline__ int render_mode(const BatchArgs& A, const CamDev& cam, int i, int j) {
+  const RayOut o = trace_ray<PREC, MODE, NB, F>(A, cam, i, j);
   const size_t px = (size_t)j * cam.nx + i;
-  if (PREC == AMR_PREC_FP64) static_cast<double*>(cam.map)[px] = o.d;
-  else static_cast<float*>(cam.map)[px] = o.f;
+  store_pixel<PREC, MODE, PARTIAL>(cam, px, o);
   if (cam.counts) cam.counts[px] = o.count;
   return o.count;
+}
+
+template <int PREC, bool NB, typename F, bool PARTIAL>
+__device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& cam, int i, int j) {
+  switch (cam.mode) {
+    case AMR_MODE_COLUMN: return render_mode<PREC, AMR_MODE_COLUMN, NB, F, PARTIAL>(A, cam, i, j);
+    case AMR_MODE_WMEAN: return render_mode<PREC, AMR_MODE_WMEAN, NB, F, PARTIAL>(A, cam, i, j);
+    case AMR_MODE_LEVEL: return render_mode<PREC, AMR_MODE_LEVEL, NB, F, PARTIAL>(A, cam, i, j);
+    default: return render_mode<PREC, AMR_MODE_MAX, NB, F, PARTIAL>(A, cam, i, j);
+  }
 }
 
 // Persistent batch kernel: each warp repeatedly takes `tiles_per_grab` ray tiles
 // from the queue head; a tile index is mapped to its camera by binary search
 // over the per-camera tile prefix sums.
-template <int PREC, bool NB, typename F>
+template <int PREC, bool NB, typename F, bool PARTIAL>
 // 56 registers: 36 resident warps per SM with 128-thread blocks (72 registers
 // allow 28, 80 allow 24).  The step loop is latency-bound per warp, so the
 // extra warps pay for the spilled words (measured: 56 beats 64, 72 and 48).
@@ -480,7 +518,7 @@ __global__ void __maxnreg__(56) batch_kernel(const BatchArgs A) {
       const int tx = lt % tiles_x, ty = lt / tiles_x;
       const int i = tx * A.tile_w + lane % A.tile_w;
       const int j = ty * A.tile_h + lane / A.tile_w;
-      if (i < cam.nx && j < cam.ny) segs += (unsigned)render_pixel<PREC, NB, F>(A, cam, i, j);
+      if (i < cam.nx && j < cam.ny) segs += (unsigned)render_pixel<PREC, NB, F, PARTIAL>(A, cam, i, j);
     }
   }
 #pragma unroll
@@ -488,40 +526,42 @@ __global__ void __maxnreg__(56) batch_kernel(const BatchArgs A) {
   if (lane == 0 && segs) atomicAdd(&A.q->segments, segs);
 }
 
-template <int PREC, bool NB, typename F>
+template <int PREC, bool NB, typename F, bool PARTIAL>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&batch_kernel<PREC, NB, F>);
+  return reinterpret_cast<const void*>(&batch_kernel<PREC, NB, F, PARTIAL>);
 }
 
-template <bool NB, typename F>
+template <bool NB, typename F, bool PARTIAL>
 const void* pick_prec(int prec) {
   switch (prec) {
-    case AMR_PREC_FP64: return kernel_ptr<AMR_PREC_FP64, NB, F>();
-    case AMR_PREC_FP32_KAHAN: return kernel_ptr<AMR_PREC_FP32_KAHAN, NB, F>();
-    default: return kernel_ptr<AMR_PREC_FP32_PLAIN, NB, F>();
+    case AMR_PREC_FP64: return kernel_ptr<AMR_PREC_FP64, NB, F, PARTIAL>();
+    case AMR_PREC_FP32_KAHAN: return kernel_ptr<AMR_PREC_FP32_KAHAN, NB, F, PARTIAL>();
+    default: return kernel_ptr<AMR_PREC_FP32_PLAIN, NB, F, PARTIAL>();
   }
 }
 
-// nb: the launch carries face-neighbour links.
-const void* pick(int prec, bool f64, bool nb) {
-  if (nb) return f64 ? pick_prec<true, double>(prec) : pick_prec<true, float>(prec);
-  return f64 ? pick_prec<false, double>(prec) : pick_prec<false, float>(prec);
+// nb: the launch carries face-neighbour links; partial: it stores accumulators
+// (only launches with links do).
+const void* pick(int prec, bool f64, bool nb, bool partial) {
+  if (nb && partial) return f64 ? pick_prec<true, double, true>(prec) : pick_prec<true, float, true>(prec);
+  if (nb) return f64 ? pick_prec<true, double, false>(prec) : pick_prec<true, float, false>(prec);
+  return f64 ? pick_prec<false, double, false>(prec) : pick_prec<false, float, false>(prec);
 }
 
 }  // namespace
 
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s) {
   void* args[] = {const_cast<BatchArgs*>(&a)};
-  return cudaLaunchKernel(pick(prec, f64, a.nbr != nullptr), dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchKernel(pick(prec, f64, a.nbr != nullptr, a.partial != 0), dim3(grid), dim3(block), args, 0, s);
 }
 
 cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, f64, nb), block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(prec, f64, nb, false), block, 0);
 }
 
 int batch_regs(int prec, bool f64, bool nb) {
   cudaFuncAttributes at{};
-  if (cudaFuncGetAttributes(&at, pick(prec, f64, nb)) != cudaSuccess) return -1;
+  if (cudaFuncGetAttributes(&at, pick(prec, f64, nb, false)) != cudaSuccess) return -1;
   return at.numRegs;
 }
 

@@ -170,3 +170,36 @@ extern "C" amr_status amr_render_batch_noalloc(int64_t n_oct, const uint64_t* re
   if (e != cudaSuccess) return amr::set_error(AMR_E_CUDA, cudaGetErrorString(e));
   return AMR_OK;
 }
+
+// Device status of the last no-allocation batch on the current device: the
+// queue blocks' error words and segment counters, read back into the caller's
+// host memory after the stream drains.  The copy lands in this function's own
+// stack, so nothing is allocated.
+extern "C" amr_status amr_noalloc_status(void* cuda_stream, int32_t* host_error, int32_t* host_oct,
+                                         uint64_t* host_segments) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return amr::set_error(AMR_E_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return failf(AMR_E_INVALID, "device %lld beyond %lld", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ready[dev]) return amr::set_error(AMR_E_INVALID, "no no-allocation batch has run on this device");
+  amr::QueueBlock q[amr::kMaxPrecisions];
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const unsigned char* scratch = static_cast<const unsigned char*>(g_scratch[dev]);
+  e = cudaMemcpyAsync(q, scratch + kQueueOff, sizeof q, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return amr::set_error(AMR_E_CUDA, cudaGetErrorString(e));
+  int32_t err = amr::kDevOk, oct = -1;
+  uint64_t segs = 0;
+  for (int g = 0; g < amr::kMaxPrecisions; ++g) {
+    segs += q[g].segments;
+    if (err == amr::kDevOk && q[g].error != amr::kDevOk) {
+      err = q[g].error;
+      oct = q[g].err_oct;
+    }
+  }
+  if (host_error) *host_error = err;
+  if (host_oct) *host_oct = oct;
+  if (host_segments) *host_segments = segs;
+  return AMR_OK;
+}

@@ -25,6 +25,14 @@ Two forms of a domain's tree:
 
 The domain split is spatial: leaves sorted by the Morton key of their centre
 (at level 22) and cut into contiguous key ranges of equal leaf count.
+
+On the GPU a domain renders its partial state directly (libamr's
+amr_render_batch_partial: each pixel's accumulators, FP32 sums as compensated
+(high, low) pairs, with rho and v read from the domain tree, foreign cells
+holding zero density) and merge_device combines the domains on the device
+(amr_merge_partials: TwoSum sums, then N / S for weighted means, max for MIP).
+merge() and merge_distributed() are the host forms over plain maps, used by
+CPU ranks.
 """
 from __future__ import annotations
 
@@ -163,6 +171,19 @@ def merge(cam: Camera, partials: Sequence[Sequence[np.ndarray]], counts: Sequenc
         num = w[0] * tot[1] + w[1] * tot[2] + w[2] * tot[3]
         out = np.divide(num, tot[0], out=np.zeros_like(num), where=tot[0] != 0)
     return out, (counts[0] if counts is not None else None)
+
+
+def merge_device(cam: Camera, partials: Sequence, stream=None):
+    """Merge the domains' partial renders of cam on the GPU (libamr's
+    amr_merge_partials: compensated TwoSum sums, max for MIP).  partials: the
+    per-domain tensors from Renderer.render_partial.  Returns the map tensor."""
+    import torch
+    from . import amr
+    dt = torch.float64 if cam.precision == amr.AMR_PREC_FP64 else torch.float32
+    out = torch.empty((cam.ny, cam.nx), dtype=dt, device=partials[0].device)
+    s = stream if stream is not None else torch.cuda.current_stream(partials[0].device)
+    amr.amr_merge_partials(cam.mode, cam.precision, cam.nx * cam.ny, list(partials), out, s.cuda_stream)
+    return out
 
 
 def merge_distributed(cam: Camera, local_partial: Sequence, group=None):

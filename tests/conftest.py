@@ -25,3 +25,10 @@ def tiny():
     from paper_1210_8014_gb300 import inputs
     tree, cams = inputs.tiny_workload()
     return tree, cams[0]
+
+
+@pytest.fixture(scope="session")
+def zoom_tree():
+    """The 193M-leaf level-22 zoom tree, generated once per test session."""
+    from paper_1210_8014_gb300 import inputs
+    return inputs.zoom_tree()

@@ -52,8 +52,8 @@ def test_batch_64_cameras_full_size(gpu):
         assert st["device_errors"] == 0
 
 
-def test_zoom_level22_full_size(gpu):
-    tree = inputs.zoom_tree()
+def test_zoom_level22_full_size(gpu, zoom_tree):
+    tree = zoom_tree
     assert tree.depth == 22 and 190e6 <= tree.n_leaves <= 210e6
     cams = inputs.zoom_cameras(tree)
     with amr.Renderer(tree) as r:
