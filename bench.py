@@ -3,14 +3,24 @@
 A step is one pass of the whole hot path over one batch: 64 cameras of uneven
 map sizes (128^2 .. 2048^2), fields of view (1 .. 1/64 of the box) and level
 cuts, mixed modes (column / weighted mean / max), rendered by one persistent
-launch fed by the ray-tile work queue, on a ~16M-leaf synthetic galaxy octree
-(levels 7-12 reached, cap 16, density + 3 velocity fields, float32), FP32
-compensated accumulation.  A segment is one leaf crossed by one ray (the sum
-of the per-pixel visited counts).  The same batch is also timed with the FP64
+launch fed by the ray-tile work queue, on a 16.0M-leaf synthetic galaxy octree
+(leaves at levels 7-12, cap 16, density + 3 velocity fields, float32), FP32
+compensated accumulation.  A segment is one leaf crossed by one ray (the sum of
+the per-pixel visited counts).  The same batch is also timed with the FP64
 kernel, and the FP32 maps are compared with the FP64 ones.
 
+The default run then measures the other workloads, each in its own record
+under "configs" (with its own clock samples): the plain-method tiny tree
+(256^2, FP64 and FP32 against the oracle), the 1024^2 galaxy precision case
+(every mode and precision, errors against the FP64 kernel and the oracle), the
+8-frame 4096^2 zoom on the 193M-leaf level-22 tree (per-frame error against
+the FP64 kernel, slice map and adaptive blur beside it) and a Poisson request
+stream at 50 req/s on the batch tree (p50/p99 latency, queue wait and render
+time).  Comparisons with the oracle belong to each record's CPU-baseline leg,
+which also times the oracle on the same sample.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config batch|precision|zoom]
+                  [--config batch|precision|zoom|serve|tiny] [--headline-only]
 
 --impl reference times the CPU oracle (plain FP64 C, all host cores) on a
 bounded sample of each step's rays.  Under torchrun (N > 1) every rank renders
@@ -35,7 +45,11 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "Gsegments/s (FP32-Kahan batch; FP64 kernel and rel err vs FP64 reported beside)"
 UNIT = "Gsegments/s"
-BYTES_PER_SEG = {0: 8, 1: 20, 2: 8}   # child word + scalars per segment, float32 fields
+# Algorithmic bytes a segment must read: the child word that says the cell is a
+# leaf at this cut (4 B) and the scalars: density (column, max), density and
+# three velocity components (wmean); float32 fields, or float64 (8 B each).
+BYTES_PER_SEG = {0: 8, 1: 20, 2: 8}
+BYTES_PER_SEG_F64 = {0: 12, 1: 36, 2: 12}
 # Essential lane operations per segment of the exact incremental step (FP32
 # compensated kernel), by mode: exit face 6, chord 5, accumulate 5, error-term
 # update 4, neighbour 4, leaf test 3, field fetch 2, count 1 = 30 (column);
@@ -60,6 +74,7 @@ def parse():
     ap.add_argument("--cams", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads' records")
     return ap.parse_args()
 
 
@@ -193,6 +208,25 @@ def recorded_traffic(config):
     return recorded_profile(config).get("dram_bytes_per_launch_full_workload")
 
 
+def recorded_compulsory(config):
+    """Compulsory bytes per launch (unique oct records and values the
+    workload's cameras touch under their cuts), counted by the oracle's
+    instrumented pass and committed as profiles/compulsory_bytes_<config>.txt;
+    None without that file."""
+    f = ROOT / "profiles" / f"compulsory_bytes_{config}.txt"
+    if not f.exists():
+        return None
+    out = {}
+    for line in f.read_text().splitlines():
+        if ":" in line and not line.lstrip().startswith("#"):
+            k, v = line.split(":", 1)
+            try:
+                out[k.strip()] = float(v.strip())
+            except ValueError:
+                pass
+    return out or None
+
+
 def dram_view(prof, ms, peak):
     """Measured DRAM traffic (ncu, per launch) as GB/s over the live kernel
     time, its fraction of the measured copy bandwidth, and the cache hit
@@ -213,6 +247,21 @@ def pipe_view(prof):
         return None
     out = {k: prof[k] for k in keys}
     out["source"] = "ncu --set full, first 8 cameras of the batch"
+    return out
+
+
+def hbm_roofline(algo_bytes, ms, config, extra=None):
+    """The kernel against HBM bandwidth: the algorithmic bytes of the launch
+    (bytes per segment x segments) over its measured time, as a fraction of
+    the measured copy bandwidth, with the ncu DRAM traffic of the same kernel
+    source (null when the source changed since the capture)."""
+    peak, kind = measured_peaks()
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": recorded_traffic(config), "peak_kind": kind + " (MEASURED_PEAKS.json hbm_gbs)",
+           "algorithmic_bytes_per_launch": algo_bytes}
+    if extra:
+        out.update(extra)
     return out
 
 
@@ -238,6 +287,57 @@ def replica_throughput(total_segments: int, ms_max: float) -> float:
     """Whole-job Gsegments/s: the segments every rank rendered in one step
     (weak scaling: a fixed batch per rank), over the slowest rank's step time."""
     return total_segments / (ms_max * 1e-3) / 1e9
+
+
+def map_errors(mode, a, b):
+    """(max, p99) error of map a against reference b: columns per pixel relative
+    (where b > 0), weighted means and mean levels normwise, max absolute."""
+    import torch
+    a = a.double()
+    b = b.double()
+    if mode == 0:
+        pos = b > 0
+        if not bool(pos.any()):
+            return 0.0, 0.0
+        rel = (a[pos] - b[pos]).abs() / b[pos]
+        return float(rel.max()), float(torch.quantile(rel[:1 << 24].float(), 0.99))
+    if mode in (1, 3):
+        s = float(b.abs().max())
+        e = (a - b).abs() / s if s > 0 else (a - b).abs()
+        return float(e.max()), float(torch.quantile(e.flatten()[:1 << 24].float(), 0.99))
+    e = float((a - b).abs().max())
+    return e, e
+
+
+# ---------------------------------------------------------------- timing helpers
+class Timer:
+    """CUDA-event timing of one launch sequence per step on `stream`, with a
+    256 MiB buffer (larger than the 129 MB L2) written on the same stream
+    before each step."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.stream = stream
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{device}")
+
+    def run(self, fn, steps, warmup=0):
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            with torch.cuda.stream(self.stream):
+                self.flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
 
 
 def _oracle_sample(oracle, lib, tree, cams, budget_s, threads, seed):
@@ -275,32 +375,67 @@ def cpu_baseline(tree, cams, budget_s=12.0, seed=0):
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": s1}}
 
 
-def aux_kernels(r, cams, stream, flush, reps=5):
+def cpu_baseline_vs_gpu(tree, cams, gpu, per_cam, seed, what):
+    """CPU-baseline leg of a workload record: the oracle on per_cam sampled
+    pixels of each camera (per_cam None: every pixel), on all host cores, timed
+    as the baseline; and the GPU maps and counts at the same pixels compared
+    with it.  gpu[k] = (map, counts) host arrays of camera k."""
+    import oracle
+    threads = os.cpu_count() or 1
+    lib = oracle.load()
+    prepared = oracle.prepare(tree)
+    rng = np.random.default_rng(seed)
+    segs, t_total, rays = 0, 0.0, 0
+    worst = {}
+    counts_equal = True
+    for cam, (gm, gc) in zip(cams, gpu):
+        if per_cam is None:
+            t0 = time.perf_counter()
+            ref, rc = oracle.render(prepared, cam, threads=threads, lib=lib)
+            t_total += time.perf_counter() - t0
+            a, c = gm, gc
+        else:
+            pi = rng.integers(0, cam.nx, per_cam)
+            pj = rng.integers(0, cam.ny, per_cam)
+            t0 = time.perf_counter()
+            ref, rc = oracle.render(prepared, cam, pixels=(pi, pj), threads=threads, lib=lib)
+            t_total += time.perf_counter() - t0
+            a, c = gm[pj, pi], gc[pj, pi]
+        segs += int(rc.sum())
+        rays += rc.size
+        counts_equal &= bool((np.asarray(c) == rc).all())
+        a = np.asarray(a, np.float64)
+        if cam.mode == 0:
+            pos = ref > 0
+            e = float((np.abs(a[pos] - ref[pos]) / ref[pos]).max(initial=0.0))
+        elif cam.mode in (1, 3):
+            s = float(np.abs(ref).max(initial=0.0))
+            e = float(np.abs(a - ref).max(initial=0.0)) / (s if s > 0 else 1.0)
+        else:
+            e = float(np.abs(a - ref).max(initial=0.0))
+        key = f"{['column', 'wmean', 'max', 'level'][cam.mode]}_{['fp64', 'fp32_kahan', 'fp32_plain'][cam.precision]}"
+        worst[key] = max(worst.get(key, 0.0), e)
+    return {"value": segs / max(t_total, 1e-9) / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{what}: {rays} rays, {segs} segments, {t_total:.2f} s of oracle time",
+            "gpu_vs_oracle": {"counts_bit_exact": counts_equal, "max_error": worst}}
+
+
+def aux_kernels(r, cams, timer, reps=5):
     """Time the slice map and the adaptive blur on one frame of the workload
     (the 4th zoom frame): slice = one descent per pixel; blur = the
     mean-level render it needs plus the two gather passes."""
     import torch
     from paper_1210_8014_gb300 import amr
     cam = cams[min(3, len(cams) - 1)]
-    dev = r.torch.device(f"cuda:{r.device}")
+    dev = torch.device(f"cuda:{r.device}")
+    stream = timer.stream
     m = torch.empty((cam.ny, cam.nx), dtype=torch.float32, device=dev)
     lv = torch.empty_like(m)
     lvl_i = torch.empty((cam.ny, cam.nx), dtype=torch.int32, device=dev)
     out = torch.empty_like(m)
 
     def timed(fn):
-        ts = []
-        for k in range(reps + 1):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            if k:
-                ts.append(e0.elapsed_time(e1))
-        return float(np.median(ts))
+        return float(np.median(timer.run(fn, reps, warmup=1)))
 
     slice_ms = timed(lambda: amr.amr_slice(r.ctx, cam, m, lvl_i, 1, stream.cuda_stream))
     level_cam = cam.with_(mode=amr.AMR_MODE_LEVEL)
@@ -336,6 +471,7 @@ def aux_kernels(r, cams, stream, flush, reps=5):
                               "taps_per_frame": taps}}
 
 
+# ---------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -378,6 +514,212 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------- other workloads
+def bench_tiny(device, steps, warmup, with_cpu):
+    """Plain-method tiny tree: 256^2 +z view at level 7, column, FP64 and FP32
+    compensated kernels; the oracle renders the whole map in the CPU leg."""
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+    tree, cams = inputs.tiny_workload()
+    cam64 = cams[0]
+    cam32 = cam64.with_(precision=amr.AMR_PREC_FP32_KAHAN)
+    r = amr.Renderer(tree, device=device)
+    stream = torch.cuda.Stream(device=device)
+    timer = Timer(device, stream)
+    out = {"workload": f"plain-method tiny tree ({tree.n_leaves} leaves, float64), +z view 256^2, level 7, column",
+           "rays": cam64.nx * cam64.ny}
+    maps = {}
+    with Clocks(device) as clk:
+        for name, cam in (("fp64", cam64), ("fp32_kahan", cam32)):
+            m, c = r.alloc(cam)
+            ts = timer.run(lambda: amr.amr_render(r.ctx, cam, m, c, 1, stream.cuda_stream), steps, warmup)
+            ms = float(np.median(ts))
+            segs = int(c.sum())
+            out[name] = {"ms_per_frame": ms, "gsegments_per_s": segs / (ms * 1e-3) / 1e9, "segments": segs,
+                         "gpu_launches": steps}
+            maps[name] = (m.cpu().numpy(), c.cpu().numpy())
+    out["clocks"] = clk.summary()
+    out["fp32_vs_fp64_err"] = map_errors(0, torch.from_numpy(maps["fp32_kahan"][0]),
+                                         torch.from_numpy(maps["fp64"][0]))[0]
+    out["note"] = "latency-bound: the tree fits in L2 (no roofline claim)"
+    r.close()
+    if with_cpu:
+        out["cpu_baseline"] = cpu_baseline_vs_gpu(tree, [cam64, cam32], [maps["fp64"], maps["fp32_kahan"]], None, 0,
+                                                  "whole 256^2 map, FP64 and FP32 kernels")
+    return out
+
+
+def bench_precision(device, steps, warmup, with_cpu):
+    """Galaxy precision case: 1024^2 random-direction whole-box view on the
+    5.6M-leaf tree, column / wmean / max, each in FP64, FP32 compensated and
+    FP32 plain; errors against the FP64 kernel (whole maps) and the oracle
+    (sampled pixels, CPU leg)."""
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+    tree = inputs.cached("galaxy_precision", inputs.galaxy_precision_tree)
+    cams = inputs.galaxy_precision_cameras(tree)
+    r = amr.Renderer(tree, device=device)
+    stream = torch.cuda.Stream(device=device)
+    timer = Timer(device, stream)
+    modes = {0: "column", 1: "wmean", 2: "max"}
+    precs = {0: "fp64", 1: "fp32_kahan", 2: "fp32_plain"}
+    res, host = {}, {}
+    with Clocks(device) as clk:
+        for cam in cams:
+            m, c = r.alloc(cam)
+            ts = timer.run(lambda: amr.amr_render(r.ctx, cam, m, c, 1, stream.cuda_stream), steps, warmup)
+            ms = float(np.median(ts))
+            segs = int(c.sum())
+            key = (cam.mode, cam.precision)
+            host[key] = (m, c)
+            res[f"{modes[cam.mode]}_{precs[cam.precision]}"] = {
+                "ms_per_frame": ms, "gsegments_per_s": segs / (ms * 1e-3) / 1e9, "segments": segs}
+    errs = {}
+    for mode in modes:
+        ref = host[(mode, 0)][0]
+        for p in (1, 2):
+            e, p99 = map_errors(mode, host[(mode, p)][0], ref)
+            errs[f"{modes[mode]}_{precs[p]}"] = {"max": e, "p99": p99}
+            assert torch.equal(host[(mode, p)][1], host[(mode, 0)][1]), "precisions visited different leaves"
+    out = {"workload": f"1024^2 random-direction view, galaxy octree {tree.n_leaves} leaves (threshold 2^-20), "
+                       f"column / wmean / max x FP64 / FP32 compensated / FP32 plain",
+           "per_mode": res, "err_vs_fp64_kernel": errs, "clocks": clk.summary(),
+           "fp32_kahan_over_fp64": {modes[m]: res[f"{modes[m]}_fp32_kahan"]["gsegments_per_s"] /
+                                    res[f"{modes[m]}_fp64"]["gsegments_per_s"] for m in modes}}
+    gpu = [(host[(c.mode, c.precision)][0].cpu().numpy(), host[(c.mode, c.precision)][1].cpu().numpy())
+           for c in cams]
+    r.close()
+    if with_cpu:
+        out["cpu_baseline"] = cpu_baseline_vs_gpu(tree, cams, gpu, 1500, 2,
+                                                  "1500 random pixels per mode and precision")
+    return out
+
+
+def bench_zoom(device, steps, warmup, with_cpu):
+    """Milky-Way scale: 8 frames of 4096^2, fov 1 -> 1/128 toward the centre
+    of the 193M-leaf level-22 tree, one persistent launch per step, FP32
+    compensated; FP64 kernel beside it; per-frame errors; slice map and
+    adaptive blur on the 4th frame."""
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+    t0 = time.perf_counter()
+    tree = inputs.cached("galaxy_zoom", inputs.zoom_tree)
+    gen_s = time.perf_counter() - t0
+    cams32 = inputs.zoom_cameras(tree)
+    cams64 = [c.with_(precision=amr.AMR_PREC_FP64) for c in cams32]
+    t0 = time.perf_counter()
+    r = amr.Renderer(tree, device=device)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=device)
+    timer = Timer(device, stream)
+    o32 = [r.alloc(c) for c in cams32]
+    o64 = [r.alloc(c) for c in cams64]
+
+    def launch(cams, outs):
+        amr.amr_render_batch(r.ctx, cams, [o[0] for o in outs], [o[1] for o in outs], 1, stream.cuda_stream)
+
+    with Clocks(device) as clk:
+        t32 = timer.run(lambda: launch(cams32, o32), steps, warmup)
+    t64 = timer.run(lambda: launch(cams64, o64), max(2, steps // 2), 1)
+    ms32, ms64 = float(np.median(t32)), float(np.median(t64))
+    seg_frame = [int(o[1].sum()) for o in o32]
+    assert seg_frame == [int(o[1].sum()) for o in o64], "FP32 and FP64 kernels visited different leaves"
+    segs = sum(seg_frame)
+    frames = []
+    for c, a, b, s in zip(cams32, o32, o64, seg_frame):
+        e, p99 = map_errors(0, a[0], b[0])
+        frames.append({"fov": c.fov[0], "level": amr.amr_camera_check(r.ctx, c), "segments": s,
+                       "max_rel_err_vs_fp64": e, "p99_rel_err_vs_fp64": p99})
+    algo = segs * BYTES_PER_SEG[0]
+    aux = aux_kernels(r, cams32, timer)
+    out = {"workload": f"8-frame 4096^2 zoom (fov 1 -> 1/128) toward the centre, column, FP32 compensated; "
+                       f"galaxy octree {tree.n_leaves} leaves, {tree.n_oct} octs, levels 7-{tree.depth}",
+           "gsegments_per_s": segs / (ms32 * 1e-3) / 1e9, "ms_per_step": ms32, "ms_per_frame": ms32 / len(cams32),
+           "segments_per_step": segs, "gpu_launches": steps,
+           "fp64_kernel": {"gsegments_per_s": segs / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64},
+           "frames": frames, "roofline": hbm_roofline(algo, ms32, "zoom"), "clocks": clk.summary(),
+           "setup_s": {"generate": gen_s, "load": load_s}, "aux_kernels": aux}
+    gpu = [(o[0].cpu().numpy(), o[1].cpu().numpy()) for o in o32]
+    del o32, o64
+    r.close()
+    torch.cuda.empty_cache()
+    if with_cpu:
+        out["cpu_baseline"] = cpu_baseline_vs_gpu(tree, cams32, gpu, 96, 4, "96 random pixels per frame")
+    return out
+
+
+def serve_stream(r, tree, seconds, device, slots=3, budget=1 << 30, max_batch=16, graph=False):
+    """Poisson 50 req/s on the batch tree through amr_submit / amr_wait: each
+    request a random-direction camera of 256^2..2048^2, fov 2^-12..1 around a
+    disk point and a random mode, delivered into page-locked host buffers (the
+    kernel writes them in place).  Latency is arrival to result."""
+    import queue as _q
+    import torch
+    from paper_1210_8014_gb300 import amr, inputs
+    reqs = inputs.request_stream(tree, duration_s=seconds)
+    amr.amr_server_config(r.ctx, slots=slots, map_budget_bytes=budget, max_batch=max_batch)
+    if graph:
+        amr.amr_set_options(r.ctx, use_graph=1)
+    # warm-up: one render of each size and mode outside the measured stream
+    for n in inputs.SIZES_SERVE:
+        for mode in (0, 1, 2):
+            c = reqs[0][1].with_(nx=n, ny=n, mode=mode)
+            amr.amr_render(r.ctx, c, np.empty((n, n), np.float32), np.empty((n, n), np.int32), 0)
+    bufs = {n: [(torch.empty((n, n), dtype=torch.float32, pin_memory=True).numpy(),
+                 torch.empty((n, n), dtype=torch.int32, pin_memory=True).numpy()) for _ in range(48)]
+            for n in inputs.SIZES_SERVE}
+    done_segments = [0]
+    waitq = _q.Queue()
+
+    def waiter():
+        while True:
+            item = waitq.get()
+            if item is None:
+                return
+            t, counts = item
+            amr.amr_wait(r.ctx, t, -1)
+            done_segments[0] += int(counts.sum())
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    use = {n: 0 for n in bufs}
+    before = r.stats()["server"]
+    with Clocks(device) as clk:
+        t0 = time.perf_counter()
+        for t_arr, cam in reqs:
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            m, c = bufs[cam.nx][use[cam.nx] % 48]
+            use[cam.nx] += 1
+            waitq.put((amr.amr_submit(r.ctx, cam, m, c), c))
+        waitq.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+    st = r.stats()["server"]
+    return {"requests": len(reqs), "wall_s": wall, "frames_per_s": (st["done"] - before["done"]) / wall,
+            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+            "queue_wait_ms": {"p50": st.get("wait_p50_ms"), "p99": st.get("wait_p99_ms")},
+            "render_ms": {"p50": st.get("service_p50_ms"), "p99": st.get("service_p99_ms")},
+            "segments_per_s": done_segments[0] / wall / 1e9, "server": st, "clocks": clk.summary(),
+            "slots": slots, "map_budget_bytes": budget, "max_batch": max_batch}
+
+
+def bench_serving(device, seconds):
+    from paper_1210_8014_gb300 import amr, inputs
+    tree = inputs.cached("galaxy_batch", inputs.batch_tree)
+    r = amr.Renderer(tree, device=device)
+    try:
+        out = serve_stream(r, tree, seconds, device)
+    finally:
+        r.close()
+    out["workload"] = (f"Poisson 50 req/s for {seconds:.0f} s on the {tree.n_leaves}-leaf galaxy octree; "
+                       f"256^2..2048^2, fov 2^-12..1, mixed modes, FP32 compensated")
+    return out
+
+
+# ---------------------------------------------------------------- headline
 def run_ours(args):
     import torch
     from paper_1210_8014_gb300 import amr, inputs
@@ -395,17 +737,18 @@ def run_ours(args):
     tree, cams32, name = workload(args.config, rank, args.cams, inputs.PREC_FP32_KAHAN)
     cams64 = [c.with_(precision=inputs.PREC_FP64) for c in cams32]
     gen_s = time.perf_counter() - t0
-    r = amr.Renderer(tree, device=device)
     t1 = time.perf_counter()
+    r = amr.Renderer(tree, device=device)       # validation, linearisation, links, upload
     torch.cuda.synchronize()
     load_s = time.perf_counter() - t1
     stream = torch.cuda.Stream(device=device)
+    timer = Timer(device, stream)
     if args.graph:
         amr.amr_set_options(r.ctx, use_graph=1)
     tuned = None
     if not args.no_autotune:
         # Tile shape, block size and queue grab picked on this batch (outside the timed region).
-        tuned, _ = amr.amr_autotune(r.ctx, cams32, reps=1)
+        tuned, _ = amr.amr_autotune(r.ctx, cams32, reps=3)
 
     def outputs(cams):
         maps = [torch.empty((c.ny, c.nx), dtype=torch.float64 if c.precision == 0 else torch.float32, device=dev)
@@ -415,7 +758,6 @@ def run_ours(args):
 
     m32, c32 = outputs(cams32)
     m64, c64 = outputs(cams64)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def launch(cams, maps, cnts):
         amr.amr_render_batch(r.ctx, cams, maps, cnts, 1, stream.cuda_stream)
@@ -428,48 +770,27 @@ def run_ours(args):
     seg_cam = [int(c.sum()) for c in c32]
     assert seg_cam == [int(c.sum()) for c in c64], "FP32 and FP64 kernels visited different leaves"
     segs = sum(seg_cam)
-    algo_bytes = sum(s * BYTES_PER_SEG[c.mode] for s, c in zip(seg_cam, cams32))
+    f64_fields = tree.fields[0].dtype == np.float64
+    bps = BYTES_PER_SEG_F64 if f64_fields else BYTES_PER_SEG
+    algo_bytes = sum(s * bps[min(c.mode, 2)] for s, c in zip(seg_cam, cams32))
     err = {"column": 0.0, "wmean": 0.0, "max": 0.0}
     per_camera = []
     for c, a, b in zip(cams32, m32, m64):
-        a = a.double()
-        if c.mode == 0:
-            pos = b > 0
-            rel = (a[pos] - b[pos]).abs() / b[pos]
-            e = float(rel.max()) if bool(pos.any()) else 0.0
-            p99 = float(torch.quantile(rel[:1 << 24].float(), 0.99)) if bool(pos.any()) else 0.0
-            err["column"] = max(err["column"], e)
-        elif c.mode == 1:
-            s = float(b.abs().max())
-            e = float((a - b).abs().max()) / s if s > 0 else 0.0
-            p99 = e
-            err["wmean"] = max(err["wmean"], e)
-        else:
-            e = float((a - b).abs().max())
-            p99 = e
-            err["max"] = max(err["max"], e)
+        e, p99 = map_errors(c.mode, a, b)
+        key = {0: "column", 1: "wmean", 2: "max"}[min(c.mode, 2)]
+        err[key] = max(err[key], e)
         per_camera.append({"mode": c.mode, "n": c.nx, "max": e, "p99": p99})
 
     def timed(cams, maps, cnts, steps):
-        times = []
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
-        for _ in range(steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            launch(cams, maps, cnts)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
+        times = timer.run(lambda: launch(cams, maps, cnts), steps)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        wall = time.perf_counter() - wall0
-        return times, wall
+        return times, time.perf_counter() - wall0
 
     with Clocks(device) as clk:
         t32, wall32 = timed(cams32, m32, c32, args.steps)
@@ -492,7 +813,8 @@ def run_ours(args):
     e2e_t = []
     h2d_before = r.stats()["h2d_bytes"]
     for _ in range(max(3, args.steps // 2)):
-        flush.fill_(1)
+        with torch.cuda.stream(stream):
+            timer.flush.fill_(1)
         torch.cuda.synchronize()
         a = time.perf_counter()
         amr.amr_render_batch(r.ctx, cams32, hmaps, hcnts, 0)
@@ -503,19 +825,26 @@ def run_ours(args):
     # pixel-offset tables), counted by the library itself
     h2d = (r.stats()["h2d_bytes"] - h2d_before) // len(e2e_t)
 
-    aux = aux_kernels(r, cams32, stream, flush) if args.config == "zoom" else None
-    peak, peak_kind = measured_peaks()
-    achieved = algo_bytes / (ms32 * 1e-3) / 1e9
-    algo_ops = sum(s_ * OPS_PER_SEG[c.mode] for s_, c in zip(seg_cam, cams32))
+    aux = aux_kernels(r, cams32, timer) if args.config == "zoom" else None
+    algo_ops = sum(s_ * OPS_PER_SEG[min(c.mode, 2)] for s_, c in zip(seg_cam, cams32))
     alu_achieved = algo_ops / (ms32 * 1e-3) / 1e12
     fp64_achieved = segs * FP64_OPS_PER_SEG / (ms64 * 1e-3) / 1e12
     stats = r.stats()
+    prof = recorded_profile(args.config)
+    roof = hbm_roofline(algo_bytes, ms32, args.config, {
+        "bytes_per_segment": bps, "compulsory": recorded_compulsory(args.config),
+        "dram": dram_view(prof, ms32, measured_peaks()[0]),
+        "alu": {"bound": "alu", "achieved": alu_achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": alu_achieved / ALU_PEAK_TOPS, "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz",
+                "ops_per_segment": OPS_PER_SEG, "algorithmic_ops_per_launch": algo_ops,
+                "pipes": pipe_view(prof)}})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
         "config": {"workload": name, "cameras": len(cams32), "rays_per_step": int(sum(c.nx * c.ny for c in cams32)),
-                   "segments_per_step": total_segs, "segments_per_step_rank0": segs, "l2": "256 MiB buffer written between timed steps",
+                   "segments_per_step": total_segs, "segments_per_step_rank0": segs,
+                   "l2": "256 MiB buffer written on the timed stream before each timed step",
                    "options": tuned or amr.amr_get_options(r.ctx).as_dict(), "parallelism": f"replicas{world}"},
         "ms_per_frame": ms32 / len(cams32),
         "fp64_kernel": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
@@ -525,15 +854,7 @@ def run_ours(args):
         "fp32_over_fp64": value / world / value64,
         "fp32_vs_fp64_err": err,
         "fp32_vs_fp64_err_per_frame": per_camera if len(cams32) <= 8 else None,
-        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                     "frac": alu_achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(args.config),
-                     "pipes": pipe_view(recorded_profile(args.config)),
-                     "peak_kind": "derived: 152 SMs x 128 lanes x 2.07 GHz", "ops_per_segment": OPS_PER_SEG,
-                     "algorithmic_ops_per_launch": algo_ops,
-                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                             "bytes_per_segment": BYTES_PER_SEG,
-                             "dram": dram_view(recorded_profile(args.config), ms32, peak)}},
+        "roofline": roof,
         "e2e": {"value": segs / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": args.steps,
@@ -543,9 +864,21 @@ def run_ours(args):
         "regs": stats.get("regs"),
         "aux_kernels": aux,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if with_cpu:
         line["cpu_baseline"] = cpu_baseline(tree, cams32)
+    del m32, c32, m64, c64
     r.close()
+    torch.cuda.empty_cache()
+    if args.config == "batch" and world == 1 and not args.headline_only:
+        sub_steps = max(3, min(args.steps, 10))
+        sub_warm = max(3, min(args.warmup, 5))
+        line["configs"] = {
+            "tiny_plain_256": bench_tiny(device, sub_steps, sub_warm, with_cpu),
+            "galaxy_precision_1024": bench_precision(device, sub_steps, sub_warm, with_cpu),
+            "zoom_level22_8x4096": bench_zoom(device, min(sub_steps, 5), 2, with_cpu),
+            "serving_poisson_50rps": bench_serving(device, 20.0),
+        }
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -553,70 +886,27 @@ def run_ours(args):
 
 
 def run_serve(args):
-    """Interactive-zoom serving: Poisson arrivals at 50 req/s on the 16M-leaf
-    batch octree, each request a random-direction camera of 256^2..2048^2 with
-    fov 2^-12..1 around a disk point and a random mode; the server admits
-    requests by free slots and map memory and batches them; latency is arrival
-    to result in the caller's host buffers."""
-    import torch
+    """Interactive-zoom serving on its own: the request stream of
+    bench_serving for --serve-seconds, as one JSON line."""
     from paper_1210_8014_gb300 import amr, inputs
-    tree = inputs.batch_tree()
-    reqs = inputs.request_stream(tree, duration_s=args.serve_seconds)
+    tree = inputs.cached("galaxy_batch", inputs.batch_tree)
     r = amr.Renderer(tree)
-    amr.amr_server_config(r.ctx, slots=3, map_budget_bytes=1 << 30, max_batch=16)
-    if args.graph:
-        amr.amr_set_options(r.ctx, use_graph=1)
-    # warm-up: one render of each size/mode outside the measured stream
-    for n in inputs.SIZES_SERVE:
-        for mode in (0, 1, 2):
-            c = reqs[0][1].with_(nx=n, ny=n, mode=mode)
-            amr.amr_render(r.ctx, c, np.empty((n, n), np.float32), np.empty((n, n), np.int32), 0)
-    # page-locked result buffers, as a serving client keeps them: the kernel
-    # writes each request's map and counts into them in place
-    bufs = {n: [(torch.empty((n, n), dtype=torch.float32, pin_memory=True).numpy(),
-                 torch.empty((n, n), dtype=torch.int32, pin_memory=True).numpy()) for _ in range(48)]
-            for n in inputs.SIZES_SERVE}
-    tickets, done_segments = [], [0]
-    import queue as _q
-    waitq = _q.Queue()
-
-    def waiter():
-        while True:
-            item = waitq.get()
-            if item is None:
-                return
-            t, counts = item
-            amr.amr_wait(r.ctx, t, -1)
-            done_segments[0] += int(counts.sum())
-
-    th = threading.Thread(target=waiter, daemon=True)
-    th.start()
-    use = {n: 0 for n in bufs}
-    with Clocks(0) as clk:
-        t0 = time.perf_counter()
-        for t_arr, cam in reqs:
-            now = time.perf_counter() - t0
-            if t_arr > now:
-                time.sleep(t_arr - now)
-            m, c = bufs[cam.nx][use[cam.nx] % 48]
-            use[cam.nx] += 1
-            tk = amr.amr_submit(r.ctx, cam, m, c)
-            waitq.put((tk, c))
-        waitq.put(None)
-        th.join()
-        wall = time.perf_counter() - t0
-    st = r.stats()["server"]
+    try:
+        st = serve_stream(r, tree, args.serve_seconds, 0, graph=args.graph)
+    finally:
+        r.close()
     line = {
-        "metric": "served frames/s at 50 req/s offered (p50/p99 latency beside)", "value": st["done"] / wall,
-        "unit": "frames/s", "n_gpus": 1, "steps": len(reqs), "warmup": 12, "ms_per_step": 1e3 * wall / len(reqs),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
+        "metric": "served frames/s at 50 req/s offered (p50/p99 latency beside)", "value": st["frames_per_s"],
+        "unit": "frames/s", "n_gpus": 1, "steps": st["requests"], "warmup": 12,
+        "ms_per_step": 1e3 * st["wall_s"] / max(1, st["requests"]), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+int64", "data": "synthetic",
         "config": {"workload": f"Poisson 50 req/s for {args.serve_seconds:.0f} s on the {tree.n_leaves}-leaf galaxy "
                                f"octree; 256^2..2048^2, fov 2^-12..1, mixed modes, FP32 compensated",
-                   "requests": len(reqs), "slots": 3, "map_budget_bytes": 1 << 30, "graph": bool(args.graph)},
-        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
-        "server": st, "segments_per_s": done_segments[0] / wall / 1e9, "clocks": clk.summary(),
+                   "requests": st["requests"], "slots": st["slots"], "map_budget_bytes": st["map_budget_bytes"],
+                   "graph": bool(args.graph)},
     }
-    r.close()
+    line.update({k: st[k] for k in ("latency_ms", "queue_wait_ms", "render_ms", "server", "segments_per_s",
+                                     "clocks")})
     print(json.dumps(line))
 
 

@@ -89,7 +89,7 @@ struct Request {
   int64_t bytes = 0;
   amr_status status = AMR_OK;
   int state = 0;  // 0 queued, 1 running, 2 done
-  std::chrono::steady_clock::time_point t_submit, t_done;
+  std::chrono::steady_clock::time_point t_submit, t_start, t_done;
   std::string err;
 };
 
@@ -139,7 +139,7 @@ struct amr_ctx {
   bool srv_started = false;
   bool srv_stop = false;
   std::vector<std::unique_ptr<ServerSlot>> srv;
-  std::vector<double> latencies_ms;
+  std::vector<double> latencies_ms, waits_ms, services_ms;  // arrival->result, arrival->admission, admission->result
   int64_t srv_batches = 0, srv_done = 0, srv_failed = 0, srv_max_inflight = 0, srv_inflight = 0;
   std::chrono::steady_clock::time_point srv_t0, srv_tlast;
 };
@@ -692,6 +692,8 @@ void complete(amr_ctx* ctx, const std::vector<std::shared_ptr<Request>>& batch, 
     if (st == AMR_OK) {
       ctx->srv_done++;
       ctx->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+      ctx->waits_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
+      ctx->services_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_start).count());
     } else {
       ctx->srv_failed++;
     }
@@ -720,6 +722,7 @@ void server_worker(amr_ctx* ctx, ServerSlot* slot) {
         if (ctx->srv_used + r->bytes > ctx->srv_budget && !(batch.empty() && ctx->srv_used == 0)) break;
         ctx->srv_used += r->bytes;
         r->state = 1;
+        r->t_start = std::chrono::steady_clock::now();
         batch.push_back(r);
         ctx->queue.pop_front();
       }
@@ -1356,17 +1359,22 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       if (s.pending && cudaEventQuery(s.done) == cudaSuccess) harvest(ctx, s);
     cudaGetLastError();
   }
-  double p50 = 0, p99 = 0, fps = 0;
+  double p50 = 0, p99 = 0, fps = 0, w50 = 0, w99 = 0, s50 = 0, s99 = 0;
   int64_t done, failed, batches, maxin, queued;
   {
     std::lock_guard<std::mutex> lk(ctx->srv_mu);
-    std::vector<double> l = ctx->latencies_ms;
-    if (!l.empty()) {
+    auto pct = [](std::vector<double> l, double* a, double* b) {
+      if (l.empty()) return;
       std::sort(l.begin(), l.end());
-      p50 = l[(size_t)(0.50 * (l.size() - 1))];
-      p99 = l[(size_t)(0.99 * (l.size() - 1))];
+      *a = l[(size_t)(0.50 * (l.size() - 1))];
+      *b = l[(size_t)(0.99 * (l.size() - 1))];
+    };
+    pct(ctx->latencies_ms, &p50, &p99);
+    pct(ctx->waits_ms, &w50, &w99);
+    pct(ctx->services_ms, &s50, &s99);
+    if (!ctx->latencies_ms.empty()) {
       const double span = std::chrono::duration<double>(ctx->srv_tlast - ctx->srv_t0).count();
-      fps = span > 0 ? l.size() / span : 0.0;
+      fps = span > 0 ? ctx->latencies_ms.size() / span : 0.0;
     }
     done = ctx->srv_done;
     failed = ctx->srv_failed;
@@ -1385,13 +1393,14 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
       "\"regs\": {\"fp64\": %d, \"fp32_kahan\": %d, \"fp32_plain\": %d}, \"sms\": %d, "
       "\"server\": {\"done\": %lld, \"failed\": %lld, \"batches\": %lld, \"max_inflight\": %lld, \"queued\": %lld, "
-      "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
+      "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"wait_p50_ms\": %.6f, \"wait_p99_ms\": %.6f, "
+      "\"service_p50_ms\": %.6f, \"service_p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
       (long long)ctx->n_h2d_bytes, (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
       (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
       o.use_graph, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
-      fps);
+      w50, w99, s50, s99, fps);
   if (len < 0) return fail(AMR_E_INVALID, "stats formatting failed");
   int64_t n = std::min<int64_t>(len, buf_len - 1);
   std::memcpy(json_buf, buf, (size_t)n);

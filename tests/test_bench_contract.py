@@ -59,7 +59,8 @@ def test_cuda_arm_line_on_the_tiny_workload():
     r = d["roofline"]
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in r, k
-    assert r["bound"] == "alu" and 0 < r["frac"] < 1.5
+    assert r["bound"] == "hbm" and 0 < r["frac"] < 1.5 and r["unit"] == "GB/s"
+    assert r["alu"]["bound"] == "alu" and 0 < r["alu"]["frac"] < 1.5
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert d["e2e"]["d2h_bytes_per_step"] == 256 * 256 * (4 + 4)     # float32 map + int32 counts
     assert d["e2e"]["h2d_bytes_per_step"] > 0
