@@ -192,16 +192,25 @@ amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t
 
 /*
  * Serving (Sec. 1: iterative interactive zoom).  amr_submit queues a request and
- * returns at once with a ticket; a server thread admits queued requests while
- * free slots and the map-memory budget allow, renders the admitted set as one
- * batch on one of several streams (so a batch admitted while others run overlaps
- * them on the device), and delivers each result into the caller's HOST buffers
- * `map` / `counts` (nullable), which must stay valid until amr_wait returns for
- * the ticket: page-locked buffers mapped into the device's address space are
- * written by the kernel in place, others through a slot buffer and a copy.  amr_wait blocks until the ticket completes or timeout_us elapses
- * (AMR_E_TIMEOUT; the request stays queued; timeout_us < 0 waits forever).
- * amr_server_config sets the slot count (concurrent batches, 1..8) and the map
- * memory budget in bytes (0 = 1 GiB); call it before the first amr_submit.
+ * returns at once with a ticket.  The server admits queued requests in arrival
+ * order while the map-memory budget allows and renders them by continuous
+ * batching at tile granularity: each launch takes at most 2^20 rays (whole ray
+ * tiles) from the admitted requests, those with the fewest tiles left first,
+ * so a request that arrives while others render joins the next launch (about
+ * a millisecond away) and small requests overtake large ones; several launch
+ * streams (slots) keep the device fed.  A request completes when its last
+ * tile lands, and its result goes into the caller's HOST buffers `map` /
+ * `counts` (nullable), which must stay valid until amr_wait returns for the
+ * ticket: page-locked buffers mapped into the device's address space are
+ * written by the kernel in place, others through staging in the server's
+ * device arena (one block of the budget's size, allocated at the first
+ * submit) and a copy.  amr_wait blocks until the ticket completes or
+ * timeout_us elapses (AMR_E_TIMEOUT; the request stays queued; timeout_us < 0
+ * waits forever).  amr_server_config sets the slot count (launches in flight,
+ * 1..8), the map memory budget in bytes (0 = 1 GiB) and the most requests one
+ * launch serves; call it before the first amr_submit.  amr_stats reports
+ * latency (arrival to result), queue wait (arrival to the first tile handed
+ * to a launch) and render time (from there to the result) as p50 / p99.
  */
 amr_status amr_server_config(amr_ctx* ctx, int32_t slots, int64_t map_budget_bytes, int32_t max_batch);
 amr_status amr_submit(amr_ctx* ctx, const amr_camera* cam, void* map, int32_t* counts, uint64_t* ticket);

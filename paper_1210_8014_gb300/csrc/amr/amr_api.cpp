@@ -88,16 +88,61 @@ struct Request {
   int32_t* counts = nullptr;
   int64_t bytes = 0;
   amr_status status = AMR_OK;
-  int state = 0;  // 0 queued, 1 running, 2 done
+  int state = 0;  // 0 queued, 1 admitted (its tiles being rendered), 2 done
   std::chrono::steady_clock::time_point t_submit, t_start, t_done;
   std::string err;
+  // Tile-granular progress once admitted: the camera with its output pointers
+  // (the caller's page-locked buffers, or staging in the server arena), its
+  // tiles, how many are handed to launches, how many are finished.
+  CamDev dev;
+  int64_t tiles = 0, next = 0, finished = 0;
+  int64_t stage_off = -1;  // arena offset of the staging, or -1 (written in place)
+  bool failed = false;
 };
 
 struct ServerSlot {
   cudaStream_t stream = nullptr;
-  void* dbuf = nullptr;
-  int64_t dcap = 0;
   std::thread th;
+};
+
+// First-fit allocator over one device block (the server's map-memory arena):
+// staging for requests whose host buffers the GPU cannot write directly.
+struct Arena {
+  char* base = nullptr;
+  int64_t size = 0;
+  std::map<int64_t, int64_t> free;  // offset -> bytes, coalesced
+  void reset(int64_t n) {
+    size = n;
+    free.clear();
+    if (n > 0) free[0] = n;
+  }
+  int64_t take(int64_t n) {
+    n = (n + 255) / 256 * 256;
+    for (auto it = free.begin(); it != free.end(); ++it) {
+      if (it->second < n) continue;
+      const int64_t off = it->first, rest = it->second - n;
+      free.erase(it);
+      if (rest) free[off + n] = rest;
+      return off;
+    }
+    return -1;
+  }
+  void give(int64_t off, int64_t n) {
+    n = (n + 255) / 256 * 256;
+    auto it = free.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free.erase(nx);
+    }
+    if (it != free.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free.erase(it);
+      }
+    }
+  }
 };
 
 }  // namespace
@@ -129,7 +174,10 @@ struct amr_ctx {
   std::condition_variable srv_cv;   // work arrived / budget freed / stop
   std::condition_variable done_cv;  // a request finished
   std::map<uint64_t, std::shared_ptr<Request>> reqs;
-  std::deque<std::shared_ptr<Request>> queue;
+  std::deque<std::shared_ptr<Request>> queue;      // submitted, not yet admitted
+  std::vector<std::shared_ptr<Request>> active;    // admitted, tiles outstanding
+  Arena arena;
+  amr_options srv_opt{};                            // launch options of every server launch
   uint64_t next_ticket = 1;
   int srv_slots = 2;
   int64_t srv_budget = int64_t(1) << 30;
@@ -426,8 +474,11 @@ amr_status check_options(const amr_options& o) {
 
 // Enqueue one batch of canonical cameras (map/count pointers already device
 // pointers) on `stream`: one persistent launch per precision present.
+// tiles (nullable): per camera, the number of tiles to render starting at its
+// tile0 (a slice of the camera); null renders every camera whole.
 amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDev>& cams,
-                   const std::vector<int>& precs, cudaStream_t stream, LaunchSlot** used, bool partial = false) {
+                   const std::vector<int>& precs, cudaStream_t stream, LaunchSlot** used, bool partial = false,
+                   const std::vector<int64_t>* tiles = nullptr) {
   std::unique_lock<std::mutex> lk(ctx->launch_mu);
   LaunchSlot& s = ctx->slots[ctx->next_slot];
   ctx->next_slot = (ctx->next_slot + 1) % ctx->slots.size();
@@ -446,7 +497,12 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   for (int p : precs) groups[p]++;
   for (int g = 0; g < amr::kMaxPrecisions; ++g) gstart[g + 1] = gstart[g] + groups[g];
   int fill[amr::kMaxPrecisions] = {gstart[0], gstart[1], gstart[2]};
-  for (int i = 0; i < n; ++i) s.h_cams[fill[precs[i]]++] = cams[i];
+  std::vector<int64_t> ntiles(n);
+  for (int i = 0; i < n; ++i) {
+    const int k = fill[precs[i]]++;
+    s.h_cams[k] = cams[i];
+    ntiles[k] = tiles ? (*tiles)[i] : tiles_of(cams[i], opt.tile_w, opt.tile_h);
+  }
   fill_offsets(s, n);
   int64_t tiles_total[amr::kMaxPrecisions] = {0, 0, 0};
   for (int g = 0; g < amr::kMaxPrecisions; ++g) {
@@ -454,7 +510,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     int64_t acc = 0;
     for (int i = 0; i < groups[g]; ++i) {
       tp[i] = (int32_t)acc;
-      acc += tiles_of(s.h_cams[gstart[g] + i], opt.tile_w, opt.tile_h);
+      acc += ntiles[gstart[g] + i];
     }
     tp[groups[g]] = (int32_t)acc;
     if (acc >= (int64_t(1) << 31) - 4096) return fail(AMR_E_INVALID, "batch too large: %lld tiles", (long long)acc);
@@ -546,7 +602,8 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
   ctx->n_renders++;
   ctx->n_cams += n;
   ctx->n_h2d_bytes += (int64_t)s.upload;
-  for (const CamDev& c : cams) ctx->n_rays += (int64_t)c.nx * c.ny;
+  for (int i = 0; i < n; ++i)
+    ctx->n_rays += tiles ? (*tiles)[i] * opt.tile_w * opt.tile_h : (int64_t)cams[i].nx * cams[i].ny;
   if (used) *used = &s;
   return AMR_OK;
 }
@@ -680,125 +737,189 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
 }
 
 // ------------------------------------------------------------------ server
-void complete(amr_ctx* ctx, const std::vector<std::shared_ptr<Request>>& batch, amr_status st, const char* err) {
-  auto now = std::chrono::steady_clock::now();
-  std::lock_guard<std::mutex> lk(ctx->srv_mu);
-  for (auto& r : batch) {
-    r->status = st;
-    if (err) r->err = err;
-    r->state = 2;
-    r->t_done = now;
-    ctx->srv_used -= r->bytes;
-    if (st == AMR_OK) {
-      ctx->srv_done++;
-      ctx->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
-      ctx->waits_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
-      ctx->services_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_start).count());
-    } else {
-      ctx->srv_failed++;
-    }
+// Rays per server launch.  A launch renders at most this many rays (whole
+// tiles) taken from the admitted requests, so a request that arrives while
+// others render joins the next launch (about a millisecond away) instead of
+// waiting behind whole batches: continuous batching at tile granularity.
+constexpr int64_t kServerLaunchRays = int64_t(1) << 20;
+
+// Deliver a finished request (srv_mu held): status, latency records, its
+// budget and arena space back.
+void finish_locked(amr_ctx* ctx, const std::shared_ptr<Request>& r, amr_status st, const std::string& err) {
+  const auto now = std::chrono::steady_clock::now();
+  r->status = st;
+  if (!err.empty()) r->err = err;
+  r->state = 2;
+  r->t_done = now;
+  ctx->srv_used -= r->bytes;
+  if (r->stage_off >= 0) {
+    ctx->arena.give(r->stage_off, r->bytes);
+    r->stage_off = -1;
   }
-  ctx->srv_inflight--;
+  if (st == AMR_OK) {
+    ctx->srv_done++;
+    ctx->latencies_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+    ctx->waits_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
+    ctx->services_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_start).count());
+  } else {
+    ctx->srv_failed++;
+  }
   ctx->srv_tlast = now;
-  ctx->done_cv.notify_all();
-  ctx->srv_cv.notify_all();
+}
+
+// Admit queued requests in arrival order while the map-memory budget allows
+// (srv_mu held).  A request whose host buffers the GPU can write (page-locked
+// and mapped) is rendered straight into them; the others get staging in the
+// server's device arena and a copy when their last tile lands.
+void admit_locked(amr_ctx* ctx) {
+  while (!ctx->queue.empty()) {
+    std::shared_ptr<Request> r = ctx->queue.front();
+    if (ctx->srv_used + r->bytes > ctx->srv_budget && ctx->srv_used > 0) return;
+    CamDev d;
+    if (canonicalise(ctx, r->cam, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h, d) != AMR_OK) {
+      ctx->queue.pop_front();
+      ctx->srv_used += r->bytes;
+      finish_locked(ctx, r, AMR_E_INVALID, g_err);
+      ctx->done_cv.notify_all();
+      continue;
+    }
+    void* m = host_alias(r->map);
+    void* c = r->counts ? host_alias(r->counts) : nullptr;
+    if (m && (c || !r->counts)) {
+      d.map = m;
+      d.counts = static_cast<int32_t*>(c);
+    } else {
+      const int64_t off = ctx->arena.take(r->bytes);
+      if (off < 0) return;  // fragmented: wait for space
+      r->stage_off = off;
+      d.map = ctx->arena.base + off;
+      d.counts = r->counts ? reinterpret_cast<int32_t*>(ctx->arena.base + off + (map_bytes(r->cam) + 255) / 256 * 256)
+                           : nullptr;
+    }
+    d.tile0 = 0;
+    r->dev = d;
+    r->tiles = tiles_of(d, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h);
+    r->state = 1;
+    ctx->srv_used += r->bytes;
+    ctx->queue.pop_front();
+    ctx->active.push_back(r);
+  }
 }
 
 void server_worker(amr_ctx* ctx, ServerSlot* slot) {
   cudaSetDevice(ctx->device);
+  const int64_t tile_px = (int64_t)ctx->srv_opt.tile_w * ctx->srv_opt.tile_h;
   for (;;) {
-    std::vector<std::shared_ptr<Request>> batch;
+    std::vector<std::shared_ptr<Request>> pr;  // the launch's pieces: request, first tile, tiles
+    std::vector<int64_t> p0, pk;
     {
       std::unique_lock<std::mutex> lk(ctx->srv_mu);
       ctx->srv_cv.wait(lk, [&] {
         if (ctx->srv_stop) return true;
-        if (ctx->queue.empty()) return false;
-        return ctx->srv_used + ctx->queue.front()->bytes <= ctx->srv_budget || ctx->srv_used == 0;
+        admit_locked(ctx);
+        for (auto& r : ctx->active)
+          if (r->next < r->tiles) return true;
+        return false;
       });
       if (ctx->srv_stop) return;
-      // Admit in arrival order while slots' memory budget allows.
-      while (!ctx->queue.empty() && (int)batch.size() < ctx->srv_max_batch) {
-        auto& r = ctx->queue.front();
-        if (ctx->srv_used + r->bytes > ctx->srv_budget && !(batch.empty() && ctx->srv_used == 0)) break;
-        ctx->srv_used += r->bytes;
-        r->state = 1;
-        r->t_start = std::chrono::steady_clock::now();
-        batch.push_back(r);
-        ctx->queue.pop_front();
+      // Shortest remaining work first: the requests with the fewest tiles not
+      // yet handed out go into the launch first, so small requests overtake
+      // large ones; at most kServerLaunchRays rays and srv_max_batch requests.
+      std::vector<std::shared_ptr<Request>> cand;
+      for (auto& r : ctx->active)
+        if (r->next < r->tiles) cand.push_back(r);
+      std::stable_sort(cand.begin(), cand.end(), [](const std::shared_ptr<Request>& a, const std::shared_ptr<Request>& b) {
+        return a->tiles - a->next < b->tiles - b->next;
+      });
+      int64_t budget = std::max<int64_t>(1, kServerLaunchRays / tile_px);
+      const auto now = std::chrono::steady_clock::now();
+      for (auto& r : cand) {
+        if (budget <= 0 || (int)pr.size() >= ctx->srv_max_batch) break;
+        const int64_t k = std::min(r->tiles - r->next, budget);
+        if (r->next == 0) r->t_start = now;
+        pr.push_back(r);
+        p0.push_back(r->next);
+        pk.push_back(k);
+        r->next += k;
+        budget -= k;
       }
       ctx->srv_batches++;
       ctx->srv_inflight++;
       ctx->srv_max_inflight = std::max(ctx->srv_max_inflight, ctx->srv_inflight);
     }
-    // Callers' page-locked buffers the GPU can address are written in place;
-    // the other requests render into this slot's buffer and are copied back.
-    int64_t need = 0;
-    std::vector<int64_t> off(batch.size());
-    std::vector<void*> hmap(batch.size(), nullptr);
-    std::vector<int32_t*> hcnt(batch.size(), nullptr);
-    for (size_t i = 0; i < batch.size(); ++i) {
-      void* m = host_alias(batch[i]->map);
-      void* c = batch[i]->counts ? host_alias(batch[i]->counts) : nullptr;
-      if (m && (c || !batch[i]->counts)) {
-        hmap[i] = m;
-        hcnt[i] = (int32_t*)c;
-        continue;
-      }
-      off[i] = need;
-      need += ((batch[i]->bytes + 255) / 256) * 256;
+    // One launch over the pieces on this slot's stream.
+    std::vector<CamDev> cams(pr.size());
+    std::vector<int> precs(pr.size());
+    for (size_t i = 0; i < pr.size(); ++i) {
+      cams[i] = pr[i]->dev;
+      cams[i].tile0 = (int32_t)p0[i];
+      precs[i] = pr[i]->cam.precision;
     }
-    amr_status st = AMR_OK;
-    std::string err;
-    if (need > slot->dcap) {
-      if (slot->dbuf) cudaFree(slot->dbuf);
-      slot->dbuf = nullptr;
-      slot->dcap = 0;
-      if (cudaMalloc(&slot->dbuf, (size_t)need) != cudaSuccess) {
-        cudaGetLastError();
-        st = AMR_E_OOM;
-        err = "server slot buffer allocation failed";
-      } else {
-        slot->dcap = need;
-      }
-    }
+    LaunchSlot* ls = nullptr;
+    amr_status st = enqueue(ctx, ctx->srv_opt, cams, precs, slot->stream, &ls, false, &pk);
+    std::string err = st == AMR_OK ? std::string() : g_err;
     if (st == AMR_OK) {
-      std::vector<amr_camera> cams(batch.size());
-      std::vector<void*> maps(batch.size());
-      std::vector<int32_t*> cnts(batch.size());
-      for (size_t i = 0; i < batch.size(); ++i) {
-        cams[i] = batch[i]->cam;
-        if (hmap[i]) {
-          maps[i] = hmap[i];
-          cnts[i] = hcnt[i];
-          continue;
-        }
-        maps[i] = (char*)slot->dbuf + off[i];
-        const int64_t mb = map_bytes(cams[i]);
-        cnts[i] = batch[i]->counts ? (int32_t*)((char*)maps[i] + ((mb + 255) / 256) * 256) : nullptr;
-      }
-      st = render_impl(ctx, (int32_t)batch.size(), cams.data(), maps.data(), cnts.data(), 1, slot->stream);
-      if (st == AMR_OK) {
-        for (size_t i = 0; i < batch.size() && st == AMR_OK; ++i) {
-          if (hmap[i]) continue;
-          if (cudaMemcpyAsync(batch[i]->map, maps[i], (size_t)map_bytes(cams[i]), cudaMemcpyDeviceToHost,
-                              slot->stream) != cudaSuccess)
-            st = AMR_E_CUDA;
-          if (cnts[i] && cudaMemcpyAsync(batch[i]->counts, cnts[i], (size_t)cams[i].nx * cams[i].ny * 4,
-                                         cudaMemcpyDeviceToHost, slot->stream) != cudaSuccess)
-            st = AMR_E_CUDA;
-        }
-        if (cudaStreamSynchronize(slot->stream) != cudaSuccess) st = AMR_E_CUDA;
-        if (st != AMR_OK) err = cudaGetErrorString(cudaGetLastError());
-      } else {
+      const cudaError_t e = cudaStreamSynchronize(slot->stream);
+      if (e != cudaSuccess) {
+        st = AMR_E_CUDA;
+        err = cudaGetErrorString(e);
+      } else if ((st = finish_sync(ctx, ls)) != AMR_OK) {
         err = g_err;
       }
     }
-    complete(ctx, batch, st, err.empty() ? nullptr : err.c_str());
+    // Progress; a request whose last tile landed is delivered.
+    std::vector<std::shared_ptr<Request>> done;
+    {
+      std::lock_guard<std::mutex> lk(ctx->srv_mu);
+      for (size_t i = 0; i < pr.size(); ++i) {
+        auto& r = pr[i];
+        if (st != AMR_OK && !r->failed) {
+          r->failed = true;
+          r->err = err;
+        }
+        r->finished += pk[i];
+        if (r->finished == r->tiles) {
+          done.push_back(r);
+          ctx->active.erase(std::find(ctx->active.begin(), ctx->active.end(), r));
+        }
+      }
+      ctx->srv_inflight--;
+    }
+    std::vector<amr_status> out(done.size(), AMR_OK);
+    for (size_t i = 0; i < done.size(); ++i) {
+      auto& r = done[i];
+      if (r->failed) {
+        out[i] = AMR_E_CUDA;
+        continue;
+      }
+      if (r->stage_off < 0) continue;
+      if (cudaMemcpyAsync(r->map, r->dev.map, (size_t)map_bytes(r->cam), cudaMemcpyDeviceToHost, slot->stream) !=
+              cudaSuccess ||
+          (r->counts && cudaMemcpyAsync(r->counts, r->dev.counts, (size_t)r->cam.nx * r->cam.ny * 4,
+                                        cudaMemcpyDeviceToHost, slot->stream) != cudaSuccess))
+        out[i] = AMR_E_CUDA;
+    }
+    if (!done.empty() && cudaStreamSynchronize(slot->stream) != cudaSuccess)
+      for (auto& o : out) o = AMR_E_CUDA;
+    {
+      std::lock_guard<std::mutex> lk(ctx->srv_mu);
+      for (size_t i = 0; i < done.size(); ++i)
+        finish_locked(ctx, done[i], out[i], out[i] == AMR_OK ? std::string() : (done[i]->err.empty() ? "CUDA error" : done[i]->err));
+    }
+    ctx->done_cv.notify_all();
+    ctx->srv_cv.notify_all();
   }
 }
 
 amr_status start_server(amr_ctx* ctx) {
   if (ctx->srv_started) return AMR_OK;
+  ctx->srv_opt = ctx->opt;
+  if (cudaMalloc((void**)&ctx->arena.base, (size_t)ctx->srv_budget) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->arena.base = nullptr;
+    return fail(AMR_E_OOM, "cannot allocate the server's %lld-byte map arena", (long long)ctx->srv_budget);
+  }
+  ctx->arena.reset(ctx->srv_budget);
   for (int i = 0; i < ctx->srv_slots; ++i) {
     auto s = std::make_unique<ServerSlot>();
     CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
@@ -980,10 +1101,20 @@ amr_status amr_destroy(amr_ctx* ctx) {
   ctx->done_cv.notify_all();
   for (auto& s : ctx->srv) {
     if (s->th.joinable()) s->th.join();
-    if (s->dbuf) cudaFree(s->dbuf);
     if (s->stream) cudaStreamDestroy(s->stream);
   }
   ctx->srv.clear();
+  {
+    // Admitted requests whose tiles were not all rendered end cancelled.
+    std::lock_guard<std::mutex> lk(ctx->srv_mu);
+    for (auto& r : ctx->active) {
+      r->status = AMR_E_CANCELLED;
+      r->state = 2;
+    }
+    ctx->active.clear();
+  }
+  ctx->done_cv.notify_all();
+  if (ctx->arena.base) cudaFree(ctx->arena.base);
   cudaDeviceSynchronize();
   for (auto& s : ctx->slots) {
     if (s.start) cudaEventDestroy(s.start);

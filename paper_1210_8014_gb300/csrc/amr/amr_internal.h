@@ -45,7 +45,7 @@ struct CamDev {
   int32_t D[3];             // quantised direction, |D_a| <= 2^23
   int32_t nx, ny, L, mode;
   int32_t tiles_x;
-  int32_t pad0;
+  int32_t tile0;            // first tile of this camera in the launch (a slice of its tiles)
   const void* rho;          // value field (column, max) or weight field (wmean)
   const void* vel[3];       // wmean velocity fields
   void* map;                // float* or double* [ny][nx]

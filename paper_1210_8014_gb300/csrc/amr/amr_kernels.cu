@@ -513,7 +513,7 @@ __global__ void __maxnreg__(56) batch_kernel(const BatchArgs A) {
         else hi = mid;
       }
       const CamDev& cam = A.cams[lo];
-      const int lt = t - __ldg(&A.tile_start[lo]);
+      const int lt = t - __ldg(&A.tile_start[lo]) + cam.tile0;
       const int tiles_x = cam.tiles_x;
       const int tx = lt % tiles_x, ty = lt / tiles_x;
       const int i = tx * A.tile_w + lane % A.tile_w;
