@@ -698,7 +698,24 @@ def serve_stream(r, tree, seconds, device, slots=3, budget=1 << 30, max_batch=16
         th.join()
         wall = time.perf_counter() - t0
     st = r.stats()["server"]
+    # The floor of each request's latency: the same request rendered alone on
+    # the idle device (device outputs, CUDA events), after the stream.
+    stream = torch.cuda.Stream(device=device)
+    solo = []
+    for _, cam in reqs:
+        m = torch.empty((cam.ny, cam.nx), dtype=torch.float32, device=f"cuda:{device}")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        amr.amr_render(r.ctx, cam, m, None, 1, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        solo.append(e0.elapsed_time(e1))
+    solo = np.array(solo)
     return {"requests": len(reqs), "wall_s": wall, "frames_per_s": (st["done"] - before["done"]) / wall,
+            "solo_render_ms": {"p50": float(np.percentile(solo, 50)), "p90": float(np.percentile(solo, 90)),
+                               "p99": float(np.percentile(solo, 99)), "max": float(solo.max()),
+                               "note": "each request rendered alone on the idle device: the latency floor"},
             "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
             "queue_wait_ms": {"p50": st.get("wait_p50_ms"), "p99": st.get("wait_p99_ms")},
             "render_ms": {"p50": st.get("service_p50_ms"), "p99": st.get("service_p99_ms")},
@@ -905,8 +922,8 @@ def run_serve(args):
                    "requests": st["requests"], "slots": st["slots"], "map_budget_bytes": st["map_budget_bytes"],
                    "graph": bool(args.graph)},
     }
-    line.update({k: st[k] for k in ("latency_ms", "queue_wait_ms", "render_ms", "server", "segments_per_s",
-                                     "clocks")})
+    line.update({k: st[k] for k in ("latency_ms", "queue_wait_ms", "render_ms", "solo_render_ms", "server",
+                                     "segments_per_s", "clocks")})
     print(json.dumps(line))
 
 

@@ -7,6 +7,8 @@ from ``amr_oracle.c`` alone, and its camera record is declared here, not taken
 from the product's headers.
 
 ``render()``     plain FP64 walk of Sec. 2.2 (C, OpenMP, exact __int128 tests).
+``touched()``    the same walk, instrumented: which leaves and refined cells a
+                 camera's rays touch (the data a frame must read at least once).
 ``bruteforce``   O(pixels x leaves) slab tests in exact integers (numpy), the
                  independent check that pins the walk on tiny trees.
 """
@@ -72,6 +74,9 @@ def load(path: Path | None = None):
     lib.oracle_slice.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.POINTER(P),
                                  ctypes.POINTER(OracleCamera), P, P, ctypes.c_int32]
     lib.oracle_slice.restype = ctypes.c_int
+    lib.oracle_touched.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.POINTER(P),
+                                   ctypes.POINTER(OracleCamera), P, P, ctypes.c_int32]
+    lib.oracle_touched.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -167,3 +172,20 @@ def slice_map(tree, cam, threads: int = 0, lib=None):
     if st != OR_OK:
         raise ValueError(f"oracle_slice failed ({st})")
     return out, lv
+
+
+def touched(tree, cam, leaf=None, inner=None, threads: int = 0, lib=None):
+    """Instrumented pass over every pixel ray of cam: boolean [n_oct, 8] masks
+    of the leaves crossed and of the refined cells descended through.  Pass
+    masks (uint8 [n_oct, 8]) to accumulate over several cameras."""
+    lib = lib or load()
+    t = prepare(tree)
+    n = t.level.shape[0]
+    leaf = np.zeros((n, 8), np.uint8) if leaf is None else leaf
+    inner = np.zeros((n, 8), np.uint8) if inner is None else inner
+    assert leaf.dtype == np.uint8 and inner.dtype == np.uint8 and leaf.flags.c_contiguous and inner.flags.c_contiguous
+    st = lib.oracle_touched(n, t.level.ctypes.data, t.coord.ctypes.data, t.child.ctypes.data, len(t.fields), t.ptrs,
+                            ctypes.byref(to_camera(cam)), leaf.ctypes.data, inner.ctypes.data, threads)
+    if st != OR_OK:
+        raise ValueError(f"oracle_touched failed ({st})")
+    return leaf, inner

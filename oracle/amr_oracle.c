@@ -181,9 +181,18 @@ typedef struct {
   int32_t n_fields;
 } otree;
 
-/* Cast one ray.  Returns OR_OK or OR_E_BADTREE (descent hit an inconsistency). */
+/* Mark a cell a ray touched (instrumented pass; marks may be NULL).  Every
+ * thread writes the same value, so the relaxed atomic store only keeps the
+ * concurrent writes well defined. */
+static void mark_cell(uint8_t* marks, int64_t oct, int c) {
+  if (marks) __atomic_store_n(&marks[8 * oct + c], (uint8_t)1, __ATOMIC_RELAXED);
+}
+
+/* Cast one ray.  Returns OR_OK or OR_E_BADTREE (descent hit an inconsistency).
+ * leaf_mark / inner_mark (nullable, [n_oct][8] bytes): set to 1 for every leaf
+ * the ray crosses and for every refined cell its descents pass through. */
 static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view* vw, const int64_t X0[3],
-                    double* out, int32_t* count) {
+                    double* out, int32_t* count, uint8_t* leaf_mark, uint8_t* inner_mark) {
   const int64_t box = (int64_t)1 << OR_K;
   *out = 0.0;
   *count = 0;
@@ -236,6 +245,7 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
       int32_t ch = tr->child[8 * oct + c];
       if (ch < 0 || lvl == vw->L) break;
       if (ch >= tr->n_oct) return OR_E_BADTREE;
+      mark_cell(inner_mark, oct, c);
       oct = ch;
       ++lvl;
     }
@@ -256,6 +266,7 @@ static int cast_ray(const otree* tr, const oracle_camera* cam, const oracle_view
     i128 num = texit.num * t.den - t.num * texit.den;
     if (num <= 0) return OR_E_BADTREE; /* cannot happen for a consistent tree */
     double len = (double)num / ((double)texit.den * (double)t.den) * vw->lambda;
+    mark_cell(leaf_mark, oct, c);
     double r = rho[8 * oct + c];
     if (cam->mode == OR_COLUMN) {
       nadd(&S, r * len);
@@ -323,7 +334,46 @@ int oracle_render(int64_t n_oct, const uint8_t* level, const int32_t* coord, con
     int j = n_pix >= 0 ? pix_j[q] : (int)(q / cam->nx);
     int64_t X0[3];
     int bad = quantised_origin(cam, i, j, X0);
-    int s = bad ? OR_E_INVALID : cast_ray(&tr, cam, &vw, X0, &map[q], &counts[q]);
+    int s = bad ? OR_E_INVALID : cast_ray(&tr, cam, &vw, X0, &map[q], &counts[q], NULL, NULL);
+    if (s != OR_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      err = s;
+    }
+  }
+  return err;
+}
+
+/*
+ * Instrumented pass: cast every pixel's ray of the camera (as oracle_render)
+ * and mark what it touches: leaf_mark[8 oct + c] = 1 for every leaf crossed
+ * (its value is read), inner_mark[8 oct + c] = 1 for every refined cell a
+ * descent passes through (its child index is read).  Counting the marks gives
+ * the data a frame must read at least once (its compulsory bytes).  Marks are
+ * only set, never cleared, so several cameras may accumulate into one array.
+ */
+int oracle_touched(int64_t n_oct, const uint8_t* level, const int32_t* coord, const int32_t* child,
+                   int32_t n_fields, const double* const* fields, const oracle_camera* cam, uint8_t* leaf_mark,
+                   uint8_t* inner_mark, int32_t n_threads) {
+  if (n_oct < 1 || !level || !coord || !child || !fields || !cam || !leaf_mark || !inner_mark) return OR_E_INVALID;
+  if (!fields_ok(cam, n_fields)) return OR_E_INVALID;
+  oracle_view vw;
+  int st = make_view(cam, tree_depth(n_oct, level), &vw);
+  if (st != OR_OK) return st;
+  otree tr = {n_oct, level, coord, child, fields, n_fields};
+  int64_t total = (int64_t)cam->nx * cam->ny;
+  int err = OR_OK;
+#ifdef _OPENMP
+  int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+#endif
+  for (int64_t q = 0; q < total; ++q) {
+    int64_t X0[3];
+    double v;
+    int32_t k;
+    int bad = quantised_origin(cam, (int)(q % cam->nx), (int)(q / cam->nx), X0);
+    int s = bad ? OR_E_INVALID : cast_ray(&tr, cam, &vw, X0, &v, &k, leaf_mark, inner_mark);
     if (s != OR_OK) {
 #ifdef _OPENMP
 #pragma omp critical

@@ -57,8 +57,9 @@ def render_leaves(tree, L: int):
     return o, c, lvl, lo, lo + size
 
 
-def bruteforce(tree, cam, pixels=None):
-    """(map, counts) by slab tests; map as float64 rounded from long double sums."""
+def bruteforce(tree, cam, pixels=None, hits_out=None):
+    """(map, counts) by slab tests; map as float64 rounded from long double sums.
+    hits_out (optional bool [n_oct, 8]): set where some pixel's ray crosses that leaf."""
     L = cut_level(cam, int(tree.level.max()))
     D = quantised_direction(cam)
     aD = np.abs(D)
@@ -99,6 +100,8 @@ def bruteforce(tree, cam, pixels=None):
                 ex_n, ex_d = np.where(earlier, a_ex, ex_n), np.where(earlier, d, ex_d)
         num = ex_n * en_d - en_n * ex_d          # (t_exit - t_entry) * ex_d * en_d
         hit = inside & (num > 0)
+        if hits_out is not None:
+            hits_out[o[hit], c[hit]] = True
         ln = num[hit].astype(np.longdouble) / (ex_d[hit].astype(np.longdouble) * en_d[hit]) * lam
         cnt[q] = int(hit.sum())
         if cam.mode == 0:

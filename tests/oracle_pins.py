@@ -314,3 +314,27 @@ def pin_slice(lib):
 
 
 ALL_PINS.append(pin_slice)
+
+
+def pin_touched(lib):
+    """Instrumented pass (compulsory bytes): the leaves it marks are exactly
+    those some pixel's ray crosses by brute-force slab tests, and the refined
+    cells it marks are exactly the proper ancestors of those leaves."""
+    for tree, cam in _bruteforce_cases()[::4]:
+        leaf, inner = oracle.touched(tree, cam, lib=lib)
+        hits = np.zeros((tree.n_oct, 8), bool)
+        bf.bruteforce(tree, cam, hits_out=hits)
+        assert hits.any() and (leaf.astype(bool) == hits).all(), ("leaves", int((leaf.astype(bool) != hits).sum()))
+        parent = {}
+        for p_, c_ in zip(*np.nonzero(tree.child >= 0)):
+            parent[int(tree.child[p_, c_])] = (int(p_), int(c_))
+        anc = np.zeros((tree.n_oct, 8), bool)
+        for o, _ in zip(*np.nonzero(hits)):
+            o = int(o)
+            while o in parent:
+                o, c = parent[o]
+                anc[o, c] = True
+        assert (inner.astype(bool) == anc).all(), ("refined cells", int((inner.astype(bool) != anc).sum()))
+
+
+ALL_PINS.append(pin_touched)

@@ -519,6 +519,29 @@ def test_server_timeout_cancel_budget_and_shutdown(gpu):
     amr.amr_destroy(ctx)
 
 
+def test_server_destroy_with_every_slot_busy(gpu):
+    """amr_destroy while three launch slots are rendering and more requests
+    wait (admitted with tiles outstanding, and queued): it returns, and the
+    device is healthy afterwards (a new context renders correctly)."""
+    tree = tree_of("galaxy")
+    big = inputs.camera_along((0.3, 0.5, 0.8), fov=1.0, n=2048, max_level=tree.depth,
+                              precision=amr.AMR_PREC_FP32_KAHAN)
+    bufs = [(torch.zeros((2048, 2048), dtype=torch.float32, pin_memory=True).numpy(),
+             torch.zeros((2048, 2048), dtype=torch.int32, pin_memory=True).numpy()) for _ in range(8)]
+    ctx = amr.amr_create(0)
+    amr.amr_load_octree(ctx, tree.n_oct, tree.level, tree.coord, tree.child, tree.fields, amr.AMR_F32)
+    amr.amr_server_config(ctx, slots=3, map_budget_bytes=1 << 30, max_batch=4)
+    tickets = [amr.amr_submit(ctx, big, m, c) for m, c in bufs]
+    amr.amr_wait(ctx, tickets[0], 60_000_000)             # work is flowing
+    st = amr.amr_stats(ctx)["server"]
+    assert st["done"] >= 1
+    amr.amr_destroy(ctx)                                  # remaining requests end cancelled
+    with amr.Renderer(tree) as r:
+        m, c = r.render(big)
+        torch.cuda.synchronize()
+        assert (host(m) == bufs[0][0]).all() and (host(c) == bufs[0][1]).all()
+
+
 def test_large_batch_grows_launch_scratch(gpu):
     """150 cameras in one batch (beyond the initial scratch of 64): every map
     equals its camera rendered alone."""

@@ -37,6 +37,8 @@ MUTANTS = {
     "slice_point_on_face_goes_low": ("c |= (X0[b] >= mid) << b;", "c |= (X0[b] > mid) << b;"),
     "slice_ignores_cut": ("if (ch < 0 || lvl == vw.L) {", "if (ch < 0) {"),
     "mean_level_off_by_one": ("nadd(&N, r * len * (double)lvl);", "nadd(&N, r * len * (double)(lvl + 1));"),
+    "touched_marks_sibling_leaf": ("mark_cell(leaf_mark, oct, c);", "mark_cell(leaf_mark, oct, c ^ 1);"),
+    "touched_marks_child_not_parent": ("mark_cell(inner_mark, oct, c);", "mark_cell(inner_mark, ch, c);"),
 }
 
 
