@@ -365,69 +365,6 @@ def test_graph_replay_matches_direct_launches(gpu):
         assert st["graph_launches"] >= 21 and 1 <= st["graph_captures"] <= 10
 
 
-def test_sortlast_domains_rendered_in_turn(gpu):
-    """Sec. 3.1 sort-last: partial maps of 3 leaf domains, rendered one after
-    another on the GPU, merge into the whole-tree GPU render."""
-    from paper_1210_8014_gb300 import sortlast
-    tree = tree_of("galaxy")
-    own = sortlast.domain_owner(tree, 3)
-    cams = [c.with_(precision=amr.AMR_PREC_FP32_KAHAN) for c in mixed_batch(tree, 6, seed=31)]
-    with amr.Renderer(tree) as r:
-        whole = [(host(m), host(c)) for m, c in r.render_batch(cams)]
-    parts = {q: [] for q in range(len(cams))}
-    counts = {q: [] for q in range(len(cams))}
-    for d in range(3):
-        for mom in (False, True):
-            sub = [q for q, c in enumerate(cams) if (c.mode == 1) == mom]
-            if not sub:
-                continue
-            with amr.Renderer(sortlast.domain_tree(tree, own, d, with_momentum=mom)) as r:
-                for q in sub:
-                    pcs = sortlast.partial_cameras(cams[q])
-                    outs = r.render_batch(pcs)
-                    parts[q].append([host(m) for m, _ in outs])
-                    counts[q].append(host(outs[0][1]))
-    for q, cam in enumerate(cams):
-        merged, mc = sortlast.merge(cam, parts[q], counts[q])
-        wm, wc = whole[q]
-        assert (mc == wc).all()
-        assert_parity(cam.mode, 1, merged, mc, wm.astype(np.float64), wc, ctx=f"sort-last camera {q}")
-
-
-def test_sortlast_pruned_subtrees_rendered_in_turn(gpu):
-    """Sort-last with pruned per-domain trees (each holds about a quarter of the
-    octs): partial maps rendered in turn on the GPU merge into the whole-tree
-    GPU render, at the pixel-rule cut and at coarser cuts."""
-    from paper_1210_8014_gb300 import sortlast
-    tree = tree_of("galaxy")
-    own = sortlast.domain_owner(tree, 4)
-    base = [c.with_(precision=amr.AMR_PREC_FP32_KAHAN) for c in mixed_batch(tree, 4, seed=41)]
-    cams = base + [c.with_(max_level=L) for c in base[:2] for L in (8, 10)]
-    with amr.Renderer(tree) as r:
-        whole = [host(m) for m, _ in r.render_batch(cams)]
-    parts = {q: [] for q in range(len(cams))}
-    for d in range(4):
-        for mom in (False, True):
-            sub = [q for q, c in enumerate(cams) if (c.mode == 1) == mom]
-            if not sub:
-                continue
-            st = sortlast.domain_subtree(tree, own, d, with_momentum=mom)
-            assert st.n_oct < 0.3 * tree.n_oct
-            with amr.Renderer(st) as r:
-                for q in sub:
-                    outs = r.render_batch(sortlast.partial_cameras(cams[q]))
-                    parts[q].append([host(m) for m, _ in outs])
-    for q, cam in enumerate(cams):
-        merged, _ = sortlast.merge(cam, parts[q])
-        wm = whole[q].astype(np.float64)
-        if cam.mode == 2:
-            assert (merged == wm).all(), q
-        else:
-            # the FP32-compensated tolerance, per pixel for columns, normwise for wmean
-            e = errors(cam.mode, merged, wm)
-            assert e["zero_ok"] and e["max"] <= TOL[1], (q, e)
-
-
 def test_slice_map_matches_oracle(gpu):
     """Slice maps (Sec. 3.3 Slicemap): values and leaf levels bit-exact."""
     tree = tree_of("galaxy")
