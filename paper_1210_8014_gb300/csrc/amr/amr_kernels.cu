@@ -330,12 +330,14 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
           v = lk.x;
           ry = (uint32_t)lk.y;
         }
-        if (v >= 0) {
-          if ((uint32_t)v >= A.n_oct) { bad = true; break; }
+        if ((uint32_t)v < A.n_oct) {
+          // The same oct, or a same-level oct (one unsigned compare also
+          // sends negative links and out-of-range indices to the rare path).
           r.y = ry;
           o = (uint32_t)v;
         } else {
           if (v == -1) break;
+          if (v >= 0) { bad = true; break; }
           // A coarser leaf: an unrefined cell, so the test below skips it.
           const int cr = -v - 2;
           if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
