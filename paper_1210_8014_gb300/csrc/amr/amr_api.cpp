@@ -416,13 +416,14 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
       if (sb & 1) { x += A1; y += A2; }
       if (sb & 2) { x -= A0; z += A2; }
       if (sb & 4) { y -= A0; z -= A1; }
-      // w: the face-link slot of the lowest stepped axis b (2b when the ray
-      // moves down b, 2b + 1 when it moves up), | 8 when several axes step.
+      // w: the face-link slot of the stepped axis b (2b when the ray moves
+      // down b, 2b + 1 when it moves up), or 7 (the corner marker) when
+      // several axes step.
       int w = 0;
       if (sb) {
         const int b = (sb & 1) ? 0 : ((sb & 2) ? 1 : 2);
         w = 2 * b + (d.D[b] < 0 ? 0 : 1);
-        if (sb & (sb - 1)) w |= 8;
+        if (sb & (sb - 1)) w = 7;
       }
       d.dF[sb] = make_int4(x, y, z, w);
     }
@@ -1154,7 +1155,8 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
     build_neighbours(rec, nb);
     // One 64-byte block per oct: its six links as 8-byte words {link, the
     // linked oct's refinement mask | level << 8} (0 beside -1), then its corner
-    // coordinates (even, < 2^22) halved and packed into 64 bits, then unused.
+    // coordinates (even, < 2^22) halved and packed into 64 bits, then the
+    // corner marker (the slot a step on several axes reads).
     std::vector<int32_t> blocks((size_t)n_oct * 16, 0);
     for (int64_t p = 0; p < n_oct; ++p) {
       for (int q = 0; q < 6; ++q) {
@@ -1168,6 +1170,7 @@ amr_status amr_load_octree(amr_ctx* ctx, int64_t n_oct, const uint8_t* level, co
       const int32_t* cc = coord + (size_t)order[p] * 3;
       const uint64_t pk = (uint64_t)(cc[0] >> 1) | ((uint64_t)(cc[1] >> 1) << 21) | ((uint64_t)(cc[2] >> 1) << 42);
       std::memcpy(&blocks[(size_t)p * 16 + 12], &pk, sizeof pk);
+      blocks[(size_t)p * 16 + 14] = amr::kCornerLink;
     }
     nb.swap(blocks);
   } catch (const std::bad_alloc&) {

@@ -13,6 +13,11 @@ constexpr int kDirBits = 23;      // bits of the largest quantised direction com
 constexpr int kMaxLevel = 22;     // deepest level an octree may hold
 constexpr int kMaxPrecisions = 3;
 
+// Slot 7 of every link block holds this marker: the increments' link slot for
+// a step on several axes at once, which leaves the oct through an edge or a
+// corner and is resolved by a descent from the root.
+constexpr int32_t kCornerLink = INT32_MIN;
+
 // Error codes a kernel writes into the work-queue block (never traps).
 enum : int32_t { kDevOk = 0, kDevBadOct = 1, kDevStepCap = 2 };
 
@@ -38,7 +43,7 @@ struct CamDev {
   int4 chordsel[3][3];
   // For each set of stepped axes (bit a: axis a): x, y, z = increments of the
   // exit-order terms F01, F02, F12 (2|D| per crossed plane); w = face-link slot
-  // of the lowest stepped axis, | 8 when more than one axis steps.
+  // of the stepped axis, or 7 (the corner marker) when more than one axis steps.
   int4 dF[8];
   // FP64 chord factor for (entry a, exit b): lamInv[a] * invD[b].
   double facD[3][3];

@@ -315,58 +315,30 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       // Neighbour at this level.  A step stays inside the oct when every
       // stepped axis moves from the oct's low cell up or from its high cell down.
       const bool inoct = ((c ^ dirbits) & stepbits) == 0;
-      if (inoct || !(dF.w & 8)) {
-        c ^= stepbits;
-        // One axis leaves the oct: its face link (the slot comes with the
-        // increments) is the same-level oct there, the coarser leaf covering
-        // that side, or -1 where the box ends.  The link carries the target
-        // oct's refinement mask and level, so a same-level step reads one
-        // 8-byte word (no dependent record load); the first-child index is
-        // read only when the ray descends.
-        int v = (int)o;
-        uint32_t ry = r.y;
-        if (!inoct) {
-          const int2 lk = __ldg(&A.nbr[o * 8u + (uint32_t)(dF.w & 7)]);
-          v = lk.x;
-          ry = (uint32_t)lk.y;
-        }
-        if ((uint32_t)v < A.n_oct) {
-          // The same oct, or a same-level oct (one unsigned compare also
-          // sends negative links and out-of-range indices to the rare path).
-          r.y = ry;
-          o = (uint32_t)v;
-        } else {
-          if (v == -1) break;
-          if (v >= 0) { bad = true; break; }
-          // A coarser leaf: an unrefined cell, so the test below skips it.
-          const int cr = -v - 2;
-          if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
-          o = (uint32_t)cr >> 3;
-          c = cr & 7;
-          r.y = ry;
-          lvl = (int)((r.y >> 8) & 31u);
-          if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
-          load_k();
-          recompute();
-        }
-        if (((r.y >> c) & 1u) && lvl < L) {
-          // The neighbour is refined: enter its child oct, go on down by mid-planes.
-          load_k();
-          const int sh = kFixBits - lvl;
-          const int ka = sel3(ea, k0, k1, k2);
-          const long long Xa = sel3(ea, X[0], X[1], X[2]);
-          m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
-          dA = sel3(ea, aD[0], aD[1], aD[2]);
-          const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
-          if (ch >= A.n_oct) { bad = true; break; }
-          o = ch;
-          r = __ldg(&rec[o]);
-          descend(lvl + 1, lvl, k0, k1, k2);
-          if (bad) break;
-          recompute();
-        }
-      } else {
+      const int cfrom = c;
+      c ^= stepbits;
+      // Leaving the oct, the step reads one 8-byte word of the oct's link
+      // block (the slot comes with the increments): the same-level oct across
+      // the face with its refinement mask and level, the coarser leaf covering
+      // that side, -1 where the box ends, or (slot 7, for steps on several axes
+      // at once) the corner marker.  A same-level step needs no record load;
+      // the first-child index is read only when the ray descends.
+      int v = (int)o;
+      uint32_t ry = r.y;
+      if (!inoct) {
+        const int2 lk = __ldg(&A.nbr[o * 8u + (uint32_t)dF.w]);
+        v = lk.x;
+        ry = (uint32_t)lk.y;
+      }
+      if ((uint32_t)v < A.n_oct) {
+        // The same oct, or a same-level oct (one unsigned compare also sends
+        // negative links, the corner marker and out-of-range indices to the
+        // rare path below).
+        r.y = ry;
+        o = (uint32_t)v;
+      } else if (v == kCornerLink) {
         // Several axes at once, leaving the oct (an edge or corner): from the root.
+        c = cfrom;
         load_k();
         const int j0 = k0 + (st0 ? s0 : 0);
         const int j1 = k1 + (st1 ? s1 : 0);
@@ -383,6 +355,36 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         descend(1, lvl, j0, j1, j2);
         if (bad) break;
         if (lvl != lvl0) recompute();
+        continue;  // the descent stopped at a leaf or the cut: nothing to enter
+      } else {
+        if (v == -1) break;
+        if (v >= 0) { bad = true; break; }
+        // A coarser leaf: an unrefined cell, so the test below skips it.
+        const int cr = -v - 2;
+        if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
+        o = (uint32_t)cr >> 3;
+        c = cr & 7;
+        r.y = ry;
+        lvl = (int)((r.y >> 8) & 31u);
+        if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
+        load_k();
+        recompute();
+      }
+      if (((r.y >> c) & 1u) && lvl < L) {
+        // The neighbour is refined: enter its child oct, go on down by mid-planes.
+        load_k();
+        const int sh = kFixBits - lvl;
+        const int ka = sel3(ea, k0, k1, k2);
+        const long long Xa = sel3(ea, X[0], X[1], X[2]);
+        m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+        dA = sel3(ea, aD[0], aD[1], aD[2]);
+        const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+        if (ch >= A.n_oct) { bad = true; break; }
+        o = ch;
+        r = __ldg(&rec[o]);
+        descend(lvl + 1, lvl, k0, k1, k2);
+        if (bad) break;
+        recompute();
       }
     } else {
       // No links: neighbour by coordinates; leaving [0, 2^lvl) ends the ray.
