@@ -221,6 +221,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
 
   descend(1, 0, 0, 0, 0);
   recompute();
+  // Refinement bits that count at the current level: all of them above the
+  // camera's cut, none at it (so the step's leaf test is one bit test).
+  uint32_t lmask = lvl < L ? 0xFFu : 0u;
 
   // ---- accumulators ---------------------------------------------------------
   double Sd = 0.0, Nd = 0.0, Md = 0.0;
@@ -330,10 +333,15 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         v = lk.x;
         ry = (uint32_t)lk.y;
       }
+      if ((uint32_t)v < A.n_oct && !(((ry & lmask) >> c) & 1u)) {
+        // The common step: the same oct, or a same-level oct, and the next
+        // cell a leaf at this cut.  Everything else (negative links, the corner
+        // marker, out-of-range indices, a refined next cell) takes one branch.
+        r.y = ry;
+        o = (uint32_t)v;
+        continue;
+      }
       if ((uint32_t)v < A.n_oct) {
-        // The same oct, or a same-level oct (one unsigned compare also sends
-        // negative links, the corner marker and out-of-range indices to the
-        // rare path below).
         r.y = ry;
         o = (uint32_t)v;
       } else if (v == kCornerLink) {
@@ -355,6 +363,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         descend(1, lvl, j0, j1, j2);
         if (bad) break;
         if (lvl != lvl0) recompute();
+        lmask = lvl < L ? 0xFFu : 0u;
         continue;  // the descent stopped at a leaf or the cut: nothing to enter
       } else {
         if (v == -1) break;
@@ -369,6 +378,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
         load_k();
         recompute();
+        lmask = 0xFFu;  // coarser than before, so above the cut
       }
       if (((r.y >> c) & 1u) && lvl < L) {
         // The neighbour is refined: enter its child oct, go on down by mid-planes.
@@ -385,6 +395,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         descend(lvl + 1, lvl, k0, k1, k2);
         if (bad) break;
         recompute();
+        lmask = lvl < L ? 0xFFu : 0u;
       }
     } else {
       // No links: neighbour by coordinates; leaving [0, 2^lvl) ends the ray.
