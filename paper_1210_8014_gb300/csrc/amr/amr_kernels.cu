@@ -318,7 +318,6 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       // Neighbour at this level.  A step stays inside the oct when every
       // stepped axis moves from the oct's low cell up or from its high cell down.
       const bool inoct = ((c ^ dirbits) & stepbits) == 0;
-      const int cfrom = c;
       c ^= stepbits;
       // Leaving the oct, the step reads one 8-byte word of the oct's link
       // block (the slot comes with the increments): the same-level oct across
@@ -346,7 +345,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         o = (uint32_t)v;
       } else if (v == kCornerLink) {
         // Several axes at once, leaving the oct (an edge or corner): from the root.
-        c = cfrom;
+        c ^= stepbits;  // back to the cell the ray leaves
         load_k();
         const int j0 = k0 + (st0 ? s0 : 0);
         const int j1 = k1 + (st1 ? s1 : 0);
@@ -371,13 +370,47 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         // A coarser leaf: an unrefined cell, so the test below skips it.
         const int cr = -v - 2;
         if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
+        const int cv = c;  // the same-level cell the step entered (no oct of that level exists there)
         o = (uint32_t)cr >> 3;
         c = cr & 7;
         r.y = ry;
         lvl = (int)((r.y >> 8) & 31u);
         if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
-        load_k();
-        recompute();
+        if (lvl == lvl0 - 1) {
+          // One level up, the common case: the coarser leaf is the parent of
+          // the cell the step entered, so on each axis its exit plane is that
+          // cell's, or one cell of the old size s farther when the cell lies in
+          // the half its parent's ray enters first (its index bit differs from
+          // the direction bit; never on an axis the ray runs parallel to).
+          // With j_a = 1 there, e' = e + s (j_a |D_b| - j_b |D_a|) exactly, so
+          // for G = E + j_a |D_b| - j_b |D_a| and the new size 2 s:
+          // E' = floor(G / 2), r' = (G & 1) s + r, i.e. F' = G | (F & 1).
+          const int nz = (aD[0] != 0 ? 1 : 0) | (aD[1] != 0 ? 2 : 0) | (aD[2] != 0 ? 4 : 0);
+          const int J = ~(cv ^ dirbits) & nz;
+          const int j0 = J & 1, j1 = (J >> 1) & 1, j2 = J >> 2;
+          const int G01 = (F01 >> 1) + j0 * aD[1] - j1 * aD[0];
+          const int G02 = (F02 >> 1) + j0 * aD[2] - j2 * aD[0];
+          const int G12 = (F12 >> 1) + j1 * aD[2] - j2 * aD[1];
+          F01 = G01 | (F01 & 1);
+          F02 = G02 | (F02 & 1);
+          F12 = G12 | (F12 & 1);
+          if (PREC == AMR_PREC_FP64) {
+            const int sh = kFixBits - lvl0;
+            r01 += (long long)(G01 & 1) << sh;
+            r02 += (long long)(G02 & 1) << sh;
+            r12 += (long long)(G12 & 1) << sh;
+          } else {
+            // r grows by s where the dropped bit is 1, s - r otherwise: sums of
+            // non-negative values, so no cancellation (one more rounding).
+            if (G01 & 1) restv[0] = __fadd_rn(restv[0], sf); else restv[1] = __fadd_rn(restv[1], sf);
+            if (G02 & 1) restv[2] = __fadd_rn(restv[2], sf); else restv[3] = __fadd_rn(restv[3], sf);
+            if (G12 & 1) restv[4] = __fadd_rn(restv[4], sf); else restv[5] = __fadd_rn(restv[5], sf);
+            sf = __fmul_rn(sf, 2.0f);
+          }
+        } else {
+          load_k();
+          recompute();
+        }
         lmask = 0xFFu;  // coarser than before, so above the cut
       }
       if (((r.y >> c) & 1u) && lvl < L) {
