@@ -7,7 +7,9 @@
 // separable: a row pass then a column pass, each output pixel using its own
 // sigma, weights exp(-k^2 / (2 sigma^2)) for |k| <= floor(3 sigma + 0.5)
 // (at most 64) renormalised over the samples inside the map; the weights come
-// from one exponential per pixel by a multiplicative recurrence.
+// from one exponential per pixel by a multiplicative recurrence.  The row pass
+// reads its taps through L1 (32 consecutive pixels of a row per warp); the
+// column pass stages 32-column tiles with their halo in shared memory.
 #include <cuda_runtime.h>
 
 #include "amr_internal.h"
@@ -102,6 +104,84 @@ __global__ void __launch_bounds__(256) blur_pass(const float* __restrict__ in, c
   out[p] = acc / norm;
 }
 
+// The column pass on tiles of 32 columns x 64 rows staged in shared memory
+// with 64 rows of halo above and below: a block of 32 x 8 threads, each
+// thread 8 pixels of its column.  Every tap is a conflict-free shared load.
+constexpr int kColTile = 64;
+__global__ void __launch_bounds__(256) blur_cols_staged(const float* __restrict__ in, const float* __restrict__ level,
+                                                        float inv_pixel, float* __restrict__ out, int nx, int ny) {
+  __shared__ float tile[(kColTile + 2 * kMaxRadius) * 32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * 32 + tx, y0 = blockIdx.y * kColTile;
+  for (int r = ty; r < kColTile + 2 * kMaxRadius; r += 8) {
+    const int gy = y0 - kMaxRadius + r;
+    tile[r * 32 + tx] = (x < nx && gy >= 0 && gy < ny) ? __ldg(&in[(size_t)gy * nx + x]) : 0.0f;
+  }
+  __syncthreads();
+  if (x >= nx) return;
+  for (int i = 0; i < kColTile / 8; ++i) {
+    const int yl = ty + 8 * i, y = y0 + yl;
+    if (y >= ny) break;
+    const float* t = tile + (yl + kMaxRadius) * 32 + tx;
+    const size_t p = (size_t)y * nx + x;
+    const float sg = sigma_of(__ldg(&level[p]), inv_pixel);
+    if (!(sg >= 0.5f)) {
+      out[p] = t[0];
+      continue;
+    }
+    const int R = min(kMaxRadius, (int)(3.0f * sg + 0.5f));
+    const float g = -0.5f / (sg * sg);
+    const float e1 = expf(g), q = e1 * e1;
+    float w = 1.0f, ratio = e1;
+    float acc = t[0], norm = 1.0f;
+    if (y - R >= 0 && y + R < ny) {
+      int k = 1;
+      for (; k + 3 <= R; k += 4) {
+        const float a0 = t[-k * 32] + t[k * 32];
+        const float a1 = t[(-k - 1) * 32] + t[(k + 1) * 32];
+        const float a2 = t[(-k - 2) * 32] + t[(k + 2) * 32];
+        const float a3 = t[(-k - 3) * 32] + t[(k + 3) * 32];
+        w *= ratio;
+        ratio *= q;
+        acc = fmaf(w, a0, acc);
+        norm = fmaf(2.0f, w, norm);
+        w *= ratio;
+        ratio *= q;
+        acc = fmaf(w, a1, acc);
+        norm = fmaf(2.0f, w, norm);
+        w *= ratio;
+        ratio *= q;
+        acc = fmaf(w, a2, acc);
+        norm = fmaf(2.0f, w, norm);
+        w *= ratio;
+        ratio *= q;
+        acc = fmaf(w, a3, acc);
+        norm = fmaf(2.0f, w, norm);
+      }
+      for (; k <= R; ++k) {
+        w *= ratio;
+        ratio *= q;
+        acc = fmaf(w, t[-k * 32] + t[k * 32], acc);
+        norm = fmaf(2.0f, w, norm);
+      }
+    } else {
+      for (int k = 1; k <= R; ++k) {
+        w *= ratio;
+        ratio *= q;
+        if (y - k >= 0) {
+          acc = fmaf(w, t[-k * 32], acc);
+          norm += w;
+        }
+        if (y + k < ny) {
+          acc = fmaf(w, t[k * 32], acc);
+          norm += w;
+        }
+      }
+    }
+    out[p] = acc / norm;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_blur(const float* in, const float* level, double pixel, float* tmp, float* out, int nx, int ny,
@@ -110,7 +190,8 @@ cudaError_t launch_blur(const float* in, const float* level, double pixel, float
   const dim3 block(256), grid((nx + 255) / 256, ny);
   const float inv_pixel = (float)(1.0 / pixel);
   blur_pass<false><<<grid, block, 0, s>>>(in, level, inv_pixel, tmp, nx, ny);
-  blur_pass<true><<<grid, block, 0, s>>>(tmp, level, inv_pixel, out, nx, ny);
+  blur_cols_staged<<<dim3((nx + 31) / 32, (ny + kColTile - 1) / kColTile), dim3(32, 8), 0, s>>>(tmp, level, inv_pixel, out,
+                                                                                              nx, ny);
   return cudaGetLastError();
 }
 
