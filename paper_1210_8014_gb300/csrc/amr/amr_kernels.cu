@@ -126,13 +126,13 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   if (!miss) miss = !(m * dO < xo * dA);
   if (miss) return res;
 
-  const int L = cam.L;
+  int L = cam.L;
   const uint2* __restrict__ rec = A.rec;
   const void* rho_base = cam.rho;
   const void* v0 = cam.vel[0];
   const void* v1 = cam.vel[1];
   const void* v2 = cam.vel[2];
-  const int s0 = D[0] > 0 ? 1 : -1, s1 = D[1] > 0 ? 1 : -1, s2 = D[2] > 0 ? 1 : -1;
+  int s0 = D[0] > 0 ? 1 : -1, s1 = D[1] > 0 ? 1 : -1, s2 = D[2] > 0 ? 1 : -1;
   // Bit a set: the ray moves down axis a (its cells are entered from the high side).
   const int dirbits = (s0 < 0 ? 1 : 0) | (s1 < 0 ? 2 : 0) | (s2 < 0 ? 4 : 0);
 
@@ -224,6 +224,28 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   // Refinement bits that count at the current level: all of them above the
   // camera's cut, none at it (so the step's leaf test is one bit test).
   uint32_t lmask = lvl < L ? 0xFFu : 0u;
+  // The ray's origin and direction are needed again only where the level
+  // changes or a step crosses an edge or a corner.  A local copy is read back
+  // there, so they are not live (in registers) across the common step.
+  volatile long long keepX[3];
+  volatile int keepD[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    keepX[a] = X[a];
+    keepD[a] = D[a];
+  }
+  auto reload = [&]() {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      X[a] = keepX[a];
+      D[a] = keepD[a];
+      aD[a] = D[a] < 0 ? -D[a] : D[a];
+    }
+    s0 = D[0] > 0 ? 1 : -1;
+    s1 = D[1] > 0 ? 1 : -1;
+    s2 = D[2] > 0 ? 1 : -1;
+    L = cam.L;
+  };
 
   // ---- accumulators ---------------------------------------------------------
   double Sd = 0.0, Nd = 0.0, Md = 0.0;
@@ -340,6 +362,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         o = (uint32_t)v;
         continue;
       }
+      reload();
       if ((uint32_t)v < A.n_oct) {
         r.y = ry;
         o = (uint32_t)v;
@@ -541,10 +564,11 @@ __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& ca
 // from the queue head; a tile index is mapped to its camera by binary search
 // over the per-camera tile prefix sums.
 template <int PREC, bool NB, typename F, bool PARTIAL>
-// 56 registers: 36 resident warps per SM with 128-thread blocks (72 registers
-// allow 28, 80 allow 24).  The step loop is latency-bound per warp, so the
-// extra warps pay for the spilled words (measured: 56 beats 64, 72 and 48).
-__global__ void __maxnreg__(56) batch_kernel(const BatchArgs A) {
+// 64 registers: 32 resident warps per SM with 128-thread blocks.  The values
+// only the level changes and edge crossings use (the ray's origin and
+// direction, the cut) are read back from a local copy there, so the common
+// step runs without spills at this cap (measured: 64 beats 56, 72 and 80).
+__global__ void __maxnreg__(64) batch_kernel(const BatchArgs A) {
   const int lane = threadIdx.x & 31;
   unsigned long long segs = 0;
   for (;;) {
