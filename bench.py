@@ -638,7 +638,8 @@ def bench_zoom(device, steps, warmup, with_cpu):
            "gsegments_per_s": segs / (ms32 * 1e-3) / 1e9, "ms_per_step": ms32, "ms_per_frame": ms32 / len(cams32),
            "segments_per_step": segs, "gpu_launches": steps,
            "fp64_kernel": {"gsegments_per_s": segs / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64},
-           "frames": frames, "roofline": hbm_roofline(algo, ms32, "zoom"), "clocks": clk.summary(),
+           "frames": frames, "roofline": hbm_roofline(algo, ms32, "zoom", {"compulsory": recorded_compulsory("zoom")}),
+           "clocks": clk.summary(),
            "setup_s": {"generate": gen_s, "load": load_s}, "aux_kernels": aux}
     gpu = [(o[0].cpu().numpy(), o[1].cpu().numpy()) for o in o32]
     del o32, o64
