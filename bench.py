@@ -421,9 +421,10 @@ def cpu_baseline_vs_gpu(tree, cams, gpu, per_cam, seed, what):
 
 
 def aux_kernels(r, cams, timer, reps=5):
-    """Time the slice map and the adaptive blur on one frame of the workload
-    (the 4th zoom frame): slice = one descent per pixel; blur = the
-    mean-level render it needs plus the two gather passes."""
+    """Time the slice map, the adaptive blur and the sort-last merge on one
+    frame of the workload (the 4th zoom frame): slice = one descent per pixel;
+    blur = the mean-level render it needs plus the two gather passes; merge =
+    eight partial renders of the frame combined on the device."""
     import torch
     from paper_1210_8014_gb300 import amr
     cam = cams[min(3, len(cams) - 1)]
@@ -458,7 +459,22 @@ def aux_kernels(r, cams, timer, reps=5):
     taps = 2.0 * float((2.0 * radius + 1.0).sum())
     l1_peak = 152 * 32 * 2.07e9 / 1e12
     blur_ttaps = taps / (blur_ms * 1e-3) / 1e12
+    # sort-last merge: eight partials of this frame (FP32 compensated column
+    # pairs, 8 B per pixel each, distinct buffers) merged on the device; it
+    # reads every partial once and writes the map
+    n_parts = 8
+    part, _ = r.render_partial([cam])[0]
+    parts = [part.clone() for _ in range(n_parts)]
+    merged = torch.empty((cam.ny, cam.nx), dtype=torch.float32, device=dev)
+    merge_ms = timed(lambda: amr.amr_merge_partials(cam.mode, cam.precision, px, parts, merged, stream.cuda_stream))
+    merge_bytes = float(px) * (n_parts * 8 + 4)
+    merge_gbs = merge_bytes / (merge_ms * 1e-3) / 1e9
+    del parts, part
     return {"frame": f"{cam.nx}^2, fov {cam.fov[0]:g}, level {amr.amr_camera_check(r.ctx, cam)}",
+            "merge_ms": merge_ms,
+            "merge_roofline": {"bound": "hbm", "achieved": merge_gbs, "peak": peak, "unit": "GB/s",
+                               "frac": merge_gbs / peak, "peak_kind": peak_kind,
+                               "bytes": merge_bytes, "partials": n_parts},
             "slice_ms": slice_ms, "slice_gpixels_per_s": px / (slice_ms * 1e-3) / 1e9,
             "slice_mean_leaf_level": depth, "level_render_ms": level_ms, "blur_ms": blur_ms,
             "blur_gpixels_per_s": px / (blur_ms * 1e-3) / 1e9,
