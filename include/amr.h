@@ -143,6 +143,14 @@ amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, void* map_out, int32_
  * precision, fed by a device work queue of ray tiles (Sec. 3.2: a master hands
  * out work to whichever worker is free).  maps[i] / counts[i] as in amr_render;
  * counts may be NULL, and so may any counts[i].
+ *
+ * Weighted-mean cameras read the weight and the three velocities of a cell as
+ * one packed 16-byte word (32 bytes for AMR_F64 fields).  The first render
+ * (here, in amr_render or by the server) that uses a given choice of weight and
+ * velocity fields builds that packed copy once: it allocates n_oct x 8 x 16 B
+ * (x 32 B) of device memory owned by the context and waits for one gather
+ * kernel; later renders reuse it, and loading a new tree frees it.  amr_stats
+ * reports the copies under tree.packed_fields / tree.packed_bytes.
  */
 amr_status amr_render_batch(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* const* maps,
                             int32_t* const* counts, int out_on_device, void* cuda_stream);

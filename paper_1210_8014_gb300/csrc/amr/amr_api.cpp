@@ -46,8 +46,17 @@ amr_status fail(amr_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(AMR_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// (density, v_x, v_y, v_z) of every cell packed for one choice of weight and
+// velocity fields: the weighted mean's step reads the four with one load.
+struct PackedFields {
+  int key[4] = {-1, -1, -1, -1};
+  void* buf = nullptr;
+  int64_t bytes = 0;
+};
+
 struct DeviceTree {
   uint2* rec = nullptr;
+  std::vector<PackedFields> packs;  // built on first use, freed with the tree
   int2* nbr = nullptr;  // [n_oct][8] 64-byte link blocks: six face links + packed coordinates
   std::vector<void*> fields;
   int64_t n_oct = 0;
@@ -154,6 +163,7 @@ struct amr_ctx {
   DeviceTree tree;
   amr_options opt{8, 4, 128, 0, 1, 0};
   std::mutex launch_mu;  // guards slots and stats
+  std::mutex pack_mu;    // guards tree.packs
   std::vector<LaunchSlot> slots;
   size_t next_slot = 0;
   void* blur_tmp = nullptr;  // intermediate of the separable blur
@@ -333,6 +343,7 @@ amr_status canonicalise_tree(const amr::TreeView& t, const amr_camera& c, int ti
   if (c.mode < AMR_MODE_COLUMN || c.mode > AMR_MODE_LEVEL) return fail(AMR_E_INVALID, "unknown mode %d", c.mode);
   if (c.precision < AMR_PREC_FP64 || c.precision > AMR_PREC_FP32_PLAIN)
     return fail(AMR_E_INVALID, "unknown precision %d", c.precision);
+  d.pack = nullptr;
   const int nf = t.n_fields;
   auto fok = [nf](int f) { return f >= 0 && f < nf; };
   if (c.mode == AMR_MODE_WMEAN) {
@@ -453,6 +464,42 @@ amr_status canonicalise(const amr_ctx* ctx, const amr_camera& c, int tile_w, int
   const DeviceTree& t = ctx->tree;
   const amr::TreeView view{t.fields.data(), (int)t.fields.size(), t.depth, t.rec != nullptr};
   return canonicalise_tree(view, c, tile_w, d);
+}
+
+// A weighted-mean camera reads (density, v_x, v_y, v_z) packed per cell: find
+// the packed array of its fields, or build it (one gather kernel on a stream of
+// its own, waited for, so every later launch on any stream sees it).
+amr_status attach_pack(amr_ctx* ctx, const amr_camera& c, CamDev& d) {
+  if (c.mode != AMR_MODE_WMEAN) return AMR_OK;
+  const int key[4] = {c.field_weight, c.field_vel[0], c.field_vel[1], c.field_vel[2]};
+  std::lock_guard<std::mutex> lk(ctx->pack_mu);
+  DeviceTree& t = ctx->tree;
+  for (const PackedFields& p : t.packs)
+    if (std::equal(key, key + 4, p.key)) {
+      d.pack = p.buf;
+      return AMR_OK;
+    }
+  const int64_t cells = t.n_oct * 8;
+  PackedFields p;
+  p.bytes = cells * 4 * (t.f64 ? 8 : 4);
+  if (cudaMalloc(&p.buf, (size_t)p.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AMR_E_OOM, "cannot allocate %lld bytes of packed weighted-mean fields", (long long)p.bytes);
+  }
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = amr::launch_pack(t.f64, t.fields[key[0]], t.fields[key[1]], t.fields[key[2]], t.fields[key[3]], p.buf, cells, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    cudaFree(p.buf);
+    return fail(AMR_E_CUDA, "packing weighted-mean fields: %s", cudaGetErrorString(e));
+  }
+  std::copy(key, key + 4, p.key);
+  t.packs.push_back(p);
+  d.pack = p.buf;
+  return AMR_OK;
 }
 
 int64_t tiles_of(const CamDev& d, int tile_w, int tile_h) {
@@ -681,6 +728,7 @@ amr_status render_impl(amr_ctx* ctx, int32_t n, const amr_camera* cams, void* co
   std::vector<int> precs(n);
   for (int i = 0; i < n; ++i) {
     amr_status st = canonicalise(ctx, cams[i], opt.tile_w, opt.tile_h, dev[i]);
+    if (st == AMR_OK) st = attach_pack(ctx, cams[i], dev[i]);
     if (st != AMR_OK) return fail(st, "camera %d: %s", i, g_err.c_str());
     if (!maps[i]) return fail(AMR_E_INVALID, "camera %d: null map pointer", i);
     precs[i] = cams[i].precision;
@@ -777,7 +825,8 @@ void admit_locked(amr_ctx* ctx) {
     std::shared_ptr<Request> r = ctx->queue.front();
     if (ctx->srv_used + r->bytes > ctx->srv_budget && ctx->srv_used > 0) return;
     CamDev d;
-    if (canonicalise(ctx, r->cam, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h, d) != AMR_OK) {
+    if (canonicalise(ctx, r->cam, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h, d) != AMR_OK ||
+        attach_pack(ctx, r->cam, d) != AMR_OK) {
       ctx->queue.pop_front();
       ctx->srv_used += r->bytes;
       finish_locked(ctx, r, AMR_E_INVALID, g_err);
@@ -1040,6 +1089,8 @@ void build_neighbours(const std::vector<uint2>& rec, std::vector<int32_t>& nb) {
 }
 
 void free_tree(DeviceTree& t) {
+  for (const PackedFields& p : t.packs)
+    if (p.buf) cudaFree(p.buf);
   if (t.rec) cudaFree(t.rec);
   if (t.nbr) cudaFree(t.nbr);
   for (void* f : t.fields) if (f) cudaFree(f);
@@ -1518,11 +1569,19 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
   }
   const amr_options& o = ctx->opt;
   const bool f64 = ctx->tree.f64;
+  int64_t packed_bytes = 0;
+  int n_packs = 0;
+  {
+    std::lock_guard<std::mutex> lk(ctx->pack_mu);
+    for (const PackedFields& p : ctx->tree.packs) packed_bytes += p.bytes;
+    n_packs = (int)ctx->tree.packs.size();
+  }
   char buf[2048];
   int len = std::snprintf(
       buf, sizeof buf,
       "{\"renders\": %lld, \"cameras\": %lld, \"rays\": %lld, \"segments\": %llu, \"h2d_bytes\": %lld, \"device_errors\": %lld, "
-      "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d}, "
+      "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d, "
+      "\"packed_fields\": %d, \"packed_bytes\": %lld}, "
       "\"options\": {\"tile_w\": %d, \"tile_h\": %d, \"block_threads\": %d, \"blocks_per_sm\": %d, "
       "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
       "\"regs\": {\"fp64\": %d, \"fp32_kahan\": %d, \"fp32_plain\": %d}, \"sms\": %d, "
@@ -1531,7 +1590,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       "\"service_p50_ms\": %.6f, \"service_p99_ms\": %.6f, \"frames_per_s\": %.6f}}",
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
       (long long)ctx->n_h2d_bytes, (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
-      (long long)ctx->tree.bytes, f64 ? 1 : 0, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
+      (long long)ctx->tree.bytes, f64 ? 1 : 0, n_packs, (long long)packed_bytes, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
       o.use_graph, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
       w50, w99, s50, s99, fps);

@@ -53,6 +53,10 @@ struct CamDev {
   int32_t tile0;            // first tile of this camera in the launch (a slice of its tiles)
   const void* rho;          // value field (column, max) or weight field (wmean)
   const void* vel[3];       // wmean velocity fields
+  // Weighted mean: (density, v_x, v_y, v_z) of every cell packed into 16
+  // bytes (32 for double fields), so a step reads its four values with one
+  // load; null when the caller gave separate arrays only.
+  const void* pack;
   void* map;                // float* or double* [ny][nx]
   int32_t* counts;          // nullable
   // Pixel-centre terms, [3 (nx + ny)] doubles: (centre + s_i u) 2^36 for each
@@ -109,6 +113,9 @@ cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int b
 // outputs; out64: double map).  err: device int set to 1 on a bad oct index.
 cudaError_t launch_slice(bool out64, bool f64, const uint2* rec, uint32_t n_oct, const CamDev* cam, int64_t n_px,
                          int32_t* err, cudaStream_t s);
+// Gather four [n_cells] fields into the packed [n_cells][4] array (float or double).
+cudaError_t launch_pack(bool f64, const void* f0, const void* f1, const void* f2, const void* f3, void* out,
+                        int64_t n_cells, cudaStream_t s);
 // Adaptive blur: row pass into tmp, column pass into out (device [ny][nx] floats).
 cudaError_t launch_blur(const float* in, const float* level, double pixel, float* tmp, float* out, int nx, int ny,
                         cudaStream_t s);

@@ -42,6 +42,24 @@ constexpr int kStepCap = 1 << 25;  // no ray at level <= 22 visits this many lea
 template <typename T>
 __device__ __forceinline__ T sel3(int i, T a, T b, T c) { return i == 0 ? a : (i == 1 ? b : c); }
 
+// (density, v_x, v_y, v_z) of one cell from the packed array: one 16-byte
+// load for float fields, two for double.
+template <typename F>
+struct Pack4 {
+  F x, y, z, w;
+};
+template <typename F>
+__device__ __forceinline__ Pack4<F> load_pack(const void* base, uint32_t cell) {
+  if constexpr (sizeof(F) == 8) {
+    const double2* p = static_cast<const double2*>(base) + 2 * (size_t)cell;
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    return {a.x, a.y, b.x, b.y};
+  } else {
+    const float4 a = __ldg(static_cast<const float4*>(base) + cell);
+    return {a.x, a.y, a.z, a.w};
+  }
+}
+
 template <typename F>
 __device__ __forceinline__ F load_field(const void* base, size_t idx) {
   return __ldg(static_cast<const F*>(base) + idx);
@@ -71,7 +89,7 @@ struct RayOut {
   int count;
 };
 
-template <int PREC, int MODE, bool NB, typename F>
+template <int PREC, int MODE, bool NB, typename F, bool PACKED = false>
 __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& cam, int i, int j) {
   RayOut res{0.0, 0.0, 0.0, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0};
 
@@ -267,7 +285,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     // 32-bit cell and link indices (n_oct * 8 < 2^31 is checked at load): one
     // 32 x 32 -> 64-bit multiply-add per address instead of 64-bit arithmetic.
     const uint32_t cell = o * 8u + (uint32_t)c;
-    const F rho = load_field<F>(rho_base, cell);
+    // A weighted mean over packed fields reads density and velocity in one load.
+    constexpr bool kPacked = PACKED && MODE == AMR_MODE_WMEAN;
+    Pack4<F> pq{};
+    if (kPacked) pq = load_pack<F>(cam.pack, cell);
+    const F rho = kPacked ? pq.x : load_field<F>(rho_base, cell);
 
     // Exit face(s): the axes whose exit time is the minimum.
     const bool lt01 = F01 < 0, gt01 = F01 > 0;
@@ -304,8 +326,10 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         const double wgt = (double)rho * len;
         Sd += wgt;
         if (MODE == AMR_MODE_WMEAN) {
-          const double vlos = (double)load_field<F>(v0, cell) * cam.w[0] + (double)load_field<F>(v1, cell) * cam.w[1] +
-                              (double)load_field<F>(v2, cell) * cam.w[2];
+          const double vlos = kPacked ? (double)pq.y * cam.w[0] + (double)pq.z * cam.w[1] + (double)pq.w * cam.w[2]
+                                      : (double)load_field<F>(v0, cell) * cam.w[0] +
+                                            (double)load_field<F>(v1, cell) * cam.w[1] +
+                                            (double)load_field<F>(v2, cell) * cam.w[2];
           Nd += wgt * vlos;
         } else if (MODE == AMR_MODE_LEVEL) {
           Nd += wgt * (double)lvl;
@@ -318,10 +342,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         if (PREC == AMR_PREC_FP32_KAHAN) kahan_add(Sf, cSf, wgt);
         else Sf = __fadd_rn(Sf, wgt);
         if (MODE == AMR_MODE_WMEAN || MODE == AMR_MODE_LEVEL) {
-          const float vlos = MODE == AMR_MODE_LEVEL
-                                 ? (float)lvl
-                                 : (float)load_field<F>(v0, cell) * cam.wF[0] + (float)load_field<F>(v1, cell) * cam.wF[1] +
-                                       (float)load_field<F>(v2, cell) * cam.wF[2];
+          const float vlos = MODE == AMR_MODE_LEVEL ? (float)lvl
+                             : kPacked ? (float)pq.y * cam.wF[0] + (float)pq.z * cam.wF[1] + (float)pq.w * cam.wF[2]
+                                       : (float)load_field<F>(v0, cell) * cam.wF[0] +
+                                             (float)load_field<F>(v1, cell) * cam.wF[1] +
+                                             (float)load_field<F>(v2, cell) * cam.wF[2];
           const float nv = __fmul_rn(wgt, vlos);
           if (PREC == AMR_PREC_FP32_KAHAN) neumaier_add(Nf, cNf, nv);
           else Nf = __fadd_rn(Nf, nv);
@@ -541,9 +566,9 @@ __device__ __forceinline__ void store_pixel(const CamDev& cam, size_t px, const 
   }
 }
 
-template <int PREC, int MODE, bool NB, typename F, bool PARTIAL>
+template <int PREC, int MODE, bool NB, typename F, bool PARTIAL, bool PACKED = false>
 __device__ __forceinline__ int render_mode(const BatchArgs& A, const CamDev& cam, int i, int j) {
-  const RayOut o = trace_ray<PREC, MODE, NB, F>(A, cam, i, j);
+  const RayOut o = trace_ray<PREC, MODE, NB, F, PACKED>(A, cam, i, j);
   const size_t px = (size_t)j * cam.nx + i;
   store_pixel<PREC, MODE, PARTIAL>(cam, px, o);
   if (cam.counts) cam.counts[px] = o.count;
@@ -554,7 +579,9 @@ template <int PREC, bool NB, typename F, bool PARTIAL>
 __device__ __forceinline__ int render_pixel(const BatchArgs& A, const CamDev& cam, int i, int j) {
   switch (cam.mode) {
     case AMR_MODE_COLUMN: return render_mode<PREC, AMR_MODE_COLUMN, NB, F, PARTIAL>(A, cam, i, j);
-    case AMR_MODE_WMEAN: return render_mode<PREC, AMR_MODE_WMEAN, NB, F, PARTIAL>(A, cam, i, j);
+    case AMR_MODE_WMEAN:
+      if (cam.pack) return render_mode<PREC, AMR_MODE_WMEAN, NB, F, PARTIAL, true>(A, cam, i, j);
+      return render_mode<PREC, AMR_MODE_WMEAN, NB, F, PARTIAL>(A, cam, i, j);
     case AMR_MODE_LEVEL: return render_mode<PREC, AMR_MODE_LEVEL, NB, F, PARTIAL>(A, cam, i, j);
     default: return render_mode<PREC, AMR_MODE_MAX, NB, F, PARTIAL>(A, cam, i, j);
   }
@@ -620,7 +647,35 @@ const void* pick(int prec, bool f64, bool nb, bool partial) {
   return f64 ? pick_prec<false, double, false>(prec) : pick_prec<false, float, false>(prec);
 }
 
+template <typename F>
+__global__ void __launch_bounds__(256) pack_kernel(const F* __restrict__ f0, const F* __restrict__ f1,
+                                                   const F* __restrict__ f2, const F* __restrict__ f3, F* out,
+                                                   int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[4 * i + 0] = f0[i];
+    out[4 * i + 1] = f1[i];
+    out[4 * i + 2] = f2[i];
+    out[4 * i + 3] = f3[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack(bool f64, const void* f0, const void* f1, const void* f2, const void* f3, void* out,
+                        int64_t n_cells, cudaStream_t s) {
+  if (n_cells <= 0) return cudaSuccess;
+  const int64_t blocks = (n_cells + 255) / 256;
+  const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+  if (f64)
+    pack_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double*>(f0), static_cast<const double*>(f1),
+                                              static_cast<const double*>(f2), static_cast<const double*>(f3),
+                                              static_cast<double*>(out), n_cells);
+  else
+    pack_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(f0), static_cast<const float*>(f1),
+                                             static_cast<const float*>(f2), static_cast<const float*>(f3),
+                                             static_cast<float*>(out), n_cells);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s) {
   void* args[] = {const_cast<BatchArgs*>(&a)};

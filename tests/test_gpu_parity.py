@@ -154,6 +154,34 @@ def test_batch_equals_alone_and_oracle(gpu):
             assert_parity(cam.mode, cam.precision, host(m1)[pj, pi], host(c1)[pj, pi], ref, rc, ctx=f"cam {q}")
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_wmean_packed_fields_per_choice(gpu, dtype):
+    """Weighted means read (weight, v_x, v_y, v_z) from a packed copy built once
+    per choice of fields: each choice matches the oracle, a repeated choice
+    reuses its copy, and loading a tree frees them."""
+    tree = inputs.random_tree(np.random.default_rng(11), depth=6, n_fields=5, dtype=dtype)
+    rng = np.random.default_rng(4)
+    base = inputs.camera_along(inputs.random_direction(rng), fov=1.0, n=(97, 61), max_level=-1,
+                               mode=amr.AMR_MODE_WMEAN)
+    choices = [(0, (1, 2, 3)), (0, (3, 1, 4)), (0, (1, 2, 3)), (0, (2, 2, 4))]
+    cell_bytes = 16 if dtype == np.float32 else 32
+    with amr.Renderer(tree) as r:
+        for k, (wf, vel) in enumerate(choices):
+            cam = base.with_(field_weight=wf, field_vel=vel)
+            ref, rc = oracle.render(tree, cam)
+            for p in PRECS:
+                m, c = r.render(cam.with_(precision=p))
+                assert_parity(1, p, host(m), host(c), ref, rc, field_is_f32=dtype == np.float32,
+                              ctx=f"choice {k} prec {p}")
+        st = r.stats()["tree"]
+        assert st["packed_fields"] == 3, st
+        assert st["packed_bytes"] == 3 * tree.n_oct * 8 * cell_bytes, st
+        amr.amr_load_octree(r.ctx, tree.n_oct, np.ascontiguousarray(tree.level, np.uint8),
+                            np.ascontiguousarray(tree.coord, np.int32), np.ascontiguousarray(tree.child, np.int32),
+                            [np.ascontiguousarray(f) for f in tree.fields], r.field_dtype)
+        assert r.stats()["tree"]["packed_fields"] == 0
+
+
 def test_segments_counter_matches_counts(gpu):
     tree = tree_of("galaxy")
     cams = mixed_batch(tree, 8, seed=3)
