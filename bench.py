@@ -174,7 +174,7 @@ def measured_peaks():
 def kernel_source_hash():
     """Hash of the batch kernel's own sources (the kernel and the structs it reads)."""
     h = hashlib.sha256()
-    for name in ("amr_kernels.cu", "amr_internal.h"):
+    for name in ("amr_trace.cuh", "amr_kernels.cu", "amr_internal.h"):
         h.update((ROOT / "paper_1210_8014_gb300" / "csrc" / "amr" / name).read_bytes())
     return h.hexdigest()[:16]
 

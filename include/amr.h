@@ -95,6 +95,9 @@ typedef struct {
   int32_t blocks_per_sm;      /* persistent grid = SMs x this (0 = occupancy limit) */
   int32_t tiles_per_grab;     /* work items a warp takes from the queue at once (>= 1) */
   int32_t use_graph;          /* replay batches through a captured CUDA graph */
+  int32_t max_regs;           /* registers per thread of the batch kernel: 0 (= 64), 56, 64 or 72;
+                                 fewer registers keep more warps resident and spill more.
+                                 Partial renders and the no-allocation entry point use 64. */
 } amr_options;
 
 /* Create a context on CUDA device `device` (allocates the work queue and a stream). */
@@ -192,8 +195,11 @@ amr_status amr_get_options(amr_ctx* ctx, amr_options* opt);
 
 /*
  * Time candidate launch configurations on this batch (each run `reps` times,
- * device results discarded) and keep the fastest in the context.  *best (nullable)
- * receives it; ms_out (nullable) its time.
+ * device results discarded) and keep the fastest in the context: the 16 launch
+ * shapes (tile 8x4, 4x8, 16x2, 32x1; 128 or 256 threads per block; 1 or 4
+ * tiles per queue grab) at the context's register cap, then the other register
+ * caps at the best shape.  *best (nullable) receives it; ms_out (nullable) its
+ * time.
  */
 amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t reps,
                         amr_options* best, double* ms_out);

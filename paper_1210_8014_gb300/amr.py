@@ -45,7 +45,8 @@ class amr_camera(ctypes.Structure):
 
 class amr_options(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("tiles_per_grab", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("tiles_per_grab", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("max_regs", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

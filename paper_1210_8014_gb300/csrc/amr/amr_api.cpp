@@ -161,7 +161,7 @@ struct amr_ctx {
   int sms = 0;
   cudaStream_t stream = nullptr;
   DeviceTree tree;
-  amr_options opt{8, 4, 128, 0, 1, 0};
+  amr_options opt{8, 4, 128, 0, 1, 0, 0};
   std::mutex launch_mu;  // guards slots and stats
   std::mutex pack_mu;    // guards tree.packs
   std::vector<LaunchSlot> slots;
@@ -178,7 +178,8 @@ struct amr_ctx {
   double last_batch_ms = 0.0;
   double autotune_ms = -1.0;
   int64_t n_graph_captures = 0, n_graph_launches = 0;
-  int occupancy[amr::kMaxPrecisions][2][33] = {};  // resident blocks per SM, by precision, dtype, block/32
+  // resident blocks per SM, by precision, dtype, register cap, block/32
+  int occupancy[amr::kMaxPrecisions][2][amr::kNumRegCaps][33] = {};
   // server
   std::mutex srv_mu;
   std::condition_variable srv_cv;   // work arrived / budget freed / stop
@@ -517,6 +518,8 @@ amr_status check_options(const amr_options& o) {
     return fail(AMR_E_INVALID, "block_threads %d: use 64..256, a multiple of 32", o.block_threads);
   if (o.blocks_per_sm < 0 || o.blocks_per_sm > 32) return fail(AMR_E_INVALID, "blocks_per_sm %d", o.blocks_per_sm);
   if (o.tiles_per_grab < 1 || o.tiles_per_grab > 64) return fail(AMR_E_INVALID, "tiles_per_grab %d", o.tiles_per_grab);
+  if (o.max_regs != 0 && o.max_regs != 56 && o.max_regs != 64 && o.max_regs != 72)
+    return fail(AMR_E_INVALID, "max_regs %d: use 0 (the default, 64), 56, 64 or 72", o.max_regs);
   return AMR_OK;
 }
 
@@ -564,7 +567,9 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     if (acc >= (int64_t(1) << 31) - 4096) return fail(AMR_E_INVALID, "batch too large: %lld tiles", (long long)acc);
     tiles_total[g] = acc;
   }
-  // Launch plan: one persistent launch per precision group present.
+  // Launch plan: one persistent launch per precision group present.  Partial
+  // renders keep the default register cap.
+  const int regs = partial || opt.max_regs == 0 ? amr::kDefaultRegs : opt.max_regs;
   amr::BatchArgs args[amr::kMaxPrecisions];
   int grids[amr::kMaxPrecisions] = {0, 0, 0};
   for (int g = 0; g < amr::kMaxPrecisions; ++g) {
@@ -585,8 +590,8 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     a.q = s.d_q + g;
     int bps = opt.blocks_per_sm;
     if (bps <= 0) {
-      int& cached = ctx->occupancy[g][ctx->tree.f64 ? 1 : 0][opt.block_threads / 32];
-      if (cached <= 0) CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, true, opt.block_threads, &cached));
+      int& cached = ctx->occupancy[g][ctx->tree.f64 ? 1 : 0][amr::reg_cap_index(regs)][opt.block_threads / 32];
+      if (cached <= 0) CUDA_TRY(amr::batch_occupancy(g, ctx->tree.f64, true, opt.block_threads, regs, &cached));
       bps = std::max(1, cached);
     }
     int64_t grid = (int64_t)ctx->sms * bps;
@@ -602,7 +607,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     // one upload: tile prefix sums, zeroed queue blocks, cameras, pixel tables
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_blob, s.h_blob, s.upload, cudaMemcpyHostToDevice, st);
     for (int g = 0; g < amr::kMaxPrecisions && e == cudaSuccess; ++g)
-      if (grids[g]) e = amr::launch_batch(g, ctx->tree.f64, args[g], grids[g], opt.block_threads, st);
+      if (grids[g]) e = amr::launch_batch(g, ctx->tree.f64, args[g], grids[g], opt.block_threads, regs, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(s.h_q, s.d_q, amr::kMaxPrecisions * sizeof(QueueBlock), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(s.done, st, ev);
@@ -615,7 +620,7 @@ amr_status enqueue(amr_ctx* ctx, const amr_options& opt, const std::vector<CamDe
     std::vector<int64_t> key = {n, partial ? 1 : 0, s.cap, (int64_t)(uintptr_t)s.d_cams, st_total, (int64_t)(uintptr_t)s.d_st,
                                 (int64_t)(uintptr_t)ctx->tree.rec,
                                 (int64_t)(uintptr_t)ctx->tree.nbr, ctx->tree.f64, opt.block_threads,
-                                opt.tile_w, opt.tile_h, opt.tiles_per_grab};
+                                opt.tile_w, opt.tile_h, opt.tiles_per_grab, regs};
     for (int g = 0; g < amr::kMaxPrecisions; ++g) {
       key.push_back(groups[g]);
       key.push_back(tiles_total[g]);
@@ -1415,34 +1420,49 @@ amr_status amr_autotune(amr_ctx* ctx, int32_t n, const amr_camera* cams, int32_t
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
+  // Median of `reps` timed runs of one candidate (a first run warms caches).
+  auto try_opt = [&](const amr_options& o) {
+    ctx->opt = o;
+    std::vector<double> times;
+    for (int r = 0; r < reps + 1 && st == AMR_OK; ++r) {
+      cudaEventRecord(e0, ctx->stream);
+      st = render_impl(ctx, n, cams, maps.data(), nullptr, 1, ctx->stream);
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(AMR_E_CUDA, "autotune sync failed");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) times.push_back(ms);
+    }
+    if (st != AMR_OK) return;
+    std::sort(times.begin(), times.end());
+    const double med = times[times.size() / 2];
+    if (med < bestms) {
+      bestms = med;
+      bestopt = o;
+    }
+  };
+  // First the launch shapes at the context's register cap, then the other
+  // caps at the best shape.
   for (auto& tl : tiles)
     for (int bt : blocks)
       for (int gr : grabs) {
+        if (st != AMR_OK) break;
         amr_options o = saved;
         o.tile_w = tl[0];
         o.tile_h = tl[1];
         o.block_threads = bt;
         o.tiles_per_grab = gr;
         o.blocks_per_sm = 0;
-        ctx->opt = o;
-        std::vector<double> times;
-        for (int r = 0; r < reps + 1 && st == AMR_OK; ++r) {
-          cudaEventRecord(e0, ctx->stream);
-          st = render_impl(ctx, n, cams, maps.data(), nullptr, 1, ctx->stream);
-          cudaEventRecord(e1, ctx->stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(AMR_E_CUDA, "autotune sync failed");
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (r > 0) times.push_back(ms);  // first run warms caches
-        }
-        if (st != AMR_OK) break;
-        std::sort(times.begin(), times.end());
-        const double med = times[times.size() / 2];
-        if (med < bestms) {
-          bestms = med;
-          bestopt = o;
-        }
+        try_opt(o);
       }
+  const int shape_regs = saved.max_regs ? saved.max_regs : amr::kDefaultRegs;
+  const amr_options best_shape = bestopt;
+  for (int regs : amr::kRegCaps) {
+    if (st != AMR_OK || regs == shape_regs) continue;
+    amr_options o = best_shape;
+    o.max_regs = regs;
+    try_opt(o);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->opt = st == AMR_OK ? bestopt : saved;
@@ -1569,6 +1589,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
   }
   const amr_options& o = ctx->opt;
   const bool f64 = ctx->tree.f64;
+  const int regs = o.max_regs ? o.max_regs : amr::kDefaultRegs;
   int64_t packed_bytes = 0;
   int n_packs = 0;
   {
@@ -1583,7 +1604,7 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       "\"last_batch_ms\": %.6f, \"tree\": {\"n_oct\": %lld, \"depth\": %d, \"device_bytes\": %lld, \"f64\": %d, "
       "\"packed_fields\": %d, \"packed_bytes\": %lld}, "
       "\"options\": {\"tile_w\": %d, \"tile_h\": %d, \"block_threads\": %d, \"blocks_per_sm\": %d, "
-      "\"tiles_per_grab\": %d, \"use_graph\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
+      "\"tiles_per_grab\": %d, \"use_graph\": %d, \"max_regs\": %d}, \"autotune_ms\": %.6f, \"graph_captures\": %lld, \"graph_launches\": %lld, "
       "\"regs\": {\"fp64\": %d, \"fp32_kahan\": %d, \"fp32_plain\": %d}, \"sms\": %d, "
       "\"server\": {\"done\": %lld, \"failed\": %lld, \"batches\": %lld, \"max_inflight\": %lld, \"queued\": %lld, "
       "\"p50_ms\": %.6f, \"p99_ms\": %.6f, \"wait_p50_ms\": %.6f, \"wait_p99_ms\": %.6f, "
@@ -1591,7 +1612,8 @@ amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len) {
       (long long)ctx->n_renders, (long long)ctx->n_cams, (long long)ctx->n_rays, ctx->n_segments,
       (long long)ctx->n_h2d_bytes, (long long)ctx->n_dev_errors, ctx->last_batch_ms, (long long)ctx->tree.n_oct, ctx->tree.depth,
       (long long)ctx->tree.bytes, f64 ? 1 : 0, n_packs, (long long)packed_bytes, o.tile_w, o.tile_h, o.block_threads, o.blocks_per_sm, o.tiles_per_grab,
-      o.use_graph, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches, amr::batch_regs(0, f64, true), amr::batch_regs(1, f64, true), amr::batch_regs(2, f64, true),
+      o.use_graph, o.max_regs, ctx->autotune_ms, (long long)ctx->n_graph_captures, (long long)ctx->n_graph_launches,
+      amr::batch_regs(0, f64, true, regs), amr::batch_regs(1, f64, true, regs), amr::batch_regs(2, f64, true, regs),
       ctx->sms, (long long)done, (long long)failed, (long long)batches, (long long)maxin, (long long)queued, p50, p99,
       w50, w99, s50, s99, fps);
   if (len < 0) return fail(AMR_E_INVALID, "stats formatting failed");

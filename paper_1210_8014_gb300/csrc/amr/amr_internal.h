@@ -107,8 +107,20 @@ int32_t canonicalise_view(const TreeView& t, const amr_camera& c, int tile_w, Ca
 // Set the calling thread's amr_last_error() message; returns st.
 int32_t set_error(int32_t st, const char* msg);
 
-// Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is double.
-cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, cudaStream_t s);
+// Register caps per thread of the batch kernel: the default, and the others
+// the map-output kernels with links are built with (amr_options.max_regs).
+constexpr int kDefaultRegs = 64;
+constexpr int kRegCaps[] = {56, 64, 72};
+constexpr int kNumRegCaps = 3;
+inline int reg_cap_index(int regs) { return regs == 56 ? 0 : (regs == 72 ? 2 : 1); }
+
+// The map-output batch kernel with links at register cap 56 or 72 (as a
+// kernel function pointer), or null for another cap.
+const void* batch_kernel_capped(int prec, bool f64, int regs);
+
+// Launch one persistent batch kernel.  prec: AMR_PREC_*; f64: field dtype is
+// double; regs: register cap (kRegCaps; others mean the default).
+cudaError_t launch_batch(int prec, bool f64, const BatchArgs& a, int grid, int block, int regs, cudaStream_t s);
 // Slice map of one camera (cam: a device CamDev whose map/counts point to the
 // outputs; out64: double map).  err: device int set to 1 on a bad oct index.
 cudaError_t launch_slice(bool out64, bool f64, const uint2* rec, uint32_t n_oct, const CamDev* cam, int64_t n_px,
@@ -120,9 +132,9 @@ cudaError_t launch_pack(bool f64, const void* f0, const void* f1, const void* f2
 cudaError_t launch_blur(const float* in, const float* level, double pixel, float* tmp, float* out, int nx, int ny,
                         cudaStream_t s);
 // Largest resident blocks per SM for the kernel of (prec, f64, with neighbour
-// links) at this block size.
-cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int* blocks_per_sm);
+// links, register cap) at this block size.
+cudaError_t batch_occupancy(int prec, bool f64, bool nb, int block, int regs, int* blocks_per_sm);
 // Registers per thread of that kernel (for stats).
-int batch_regs(int prec, bool f64, bool nb);
+int batch_regs(int prec, bool f64, bool nb, int regs);
 
 }  // namespace amr

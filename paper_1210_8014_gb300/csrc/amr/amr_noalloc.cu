@@ -160,12 +160,12 @@ extern "C" amr_status amr_render_batch_noalloc(int64_t n_oct, const uint64_t* re
     a.tiles_per_grab = 1;
     a.q = d_q + g;
     int bps = 1;
-    e = amr::batch_occupancy(g, f64, false, block, &bps);
+    e = amr::batch_occupancy(g, f64, false, block, amr::kDefaultRegs, &bps);
     if (e != cudaSuccess) break;
     const int64_t blocks_needed = (total[g] * 32 + block - 1) / block;
     int64_t grid = (int64_t)sms * (bps > 0 ? bps : 1);
     grid = grid < blocks_needed ? grid : blocks_needed;
-    e = amr::launch_batch(g, f64, a, (int)(grid > 0 ? grid : 1), block, stream);
+    e = amr::launch_batch(g, f64, a, (int)(grid > 0 ? grid : 1), block, amr::kDefaultRegs, stream);
   }
   if (e != cudaSuccess) return amr::set_error(AMR_E_CUDA, cudaGetErrorString(e));
   return AMR_OK;

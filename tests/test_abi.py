@@ -40,7 +40,7 @@ def test_amr_h_declares_the_boundary():
 def test_camera_struct_layout_matches_header():
     from paper_1210_8014_gb300 import amr
     assert ctypes.sizeof(amr.amr_camera) == 14 * 8 + 10 * 4
-    assert ctypes.sizeof(amr.amr_options) == 6 * 4
+    assert ctypes.sizeof(amr.amr_options) == 7 * 4
 
 
 def test_calls_fail_cleanly_without_a_device():

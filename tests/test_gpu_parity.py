@@ -326,10 +326,36 @@ def test_autotune_keeps_results(gpu):
         a = r.render_batch(cams)
         best, ms = amr.amr_autotune(r.ctx, cams, reps=1)
         assert best["tile_w"] * best["tile_h"] == 32 and ms > 0
+        assert best["max_regs"] in (0, 56, 64, 72)
+        assert amr.amr_get_options(r.ctx).as_dict() == best
         b = r.render_batch(cams)
         torch.cuda.synchronize()
         for x, y in zip(a, b):
             assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1])
+
+
+def test_register_caps_give_identical_maps(gpu):
+    """The register cap (56, 64, 72 per thread) changes occupancy and spills,
+    not arithmetic: every cap renders the mixed batch bit for bit alike, the
+    FP64 kernel included; other caps are rejected."""
+    tree = tree_of("galaxy")
+    cams = mixed_batch(tree, 12, seed=9)
+    with amr.Renderer(tree) as r:
+        ref = r.render_batch(cams)
+        torch.cuda.synchronize()
+        for regs in (56, 72, 64, 0):
+            amr.amr_set_options(r.ctx, max_regs=regs)
+            out = r.render_batch(cams)
+            torch.cuda.synchronize()
+            st = r.stats()
+            assert st["options"]["max_regs"] == regs
+            assert all(0 < v <= (regs or 64) for v in st["regs"].values()), st["regs"]
+            for q, (x, y) in enumerate(zip(ref, out)):
+                assert torch.equal(x[1], y[1]), f"cap {regs} camera {q}: counts differ"
+                assert torch.equal(x[0], y[0]), f"cap {regs} camera {q}: maps differ"
+        for bad in (48, 60, 80, -1):
+            with pytest.raises(amr.AmrError):
+                amr.amr_set_options(r.ctx, max_regs=bad)
 
 
 def test_server_alone_vs_mix(gpu):
