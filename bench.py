@@ -565,11 +565,13 @@ def bench_tiny(device, steps, warmup, with_cpu):
     return out
 
 
-def bench_precision(device, steps, warmup, with_cpu):
+def bench_precision(device, steps, warmup, with_cpu, tune=True):
     """Galaxy precision case: 1024^2 random-direction whole-box view on the
     5.6M-leaf tree, column / wmean / max, each in FP64, FP32 compensated and
     FP32 plain; errors against the FP64 kernel (whole maps) and the oracle
-    (sampled pixels, CPU leg)."""
+    (sampled pixels, CPU leg).  With tune, each (mode, precision) frame is
+    timed with the launch configuration the autotuner picks for it (the best
+    register cap differs between modes)."""
     import torch
     from paper_1210_8014_gb300 import amr, inputs
     tree = inputs.cached("galaxy_precision", inputs.galaxy_precision_tree)
@@ -583,13 +585,15 @@ def bench_precision(device, steps, warmup, with_cpu):
     with Clocks(device) as clk:
         for cam in cams:
             m, c = r.alloc(cam)
+            opts = amr.amr_autotune(r.ctx, [cam], reps=3)[0] if tune else amr.amr_get_options(r.ctx).as_dict()
             ts = timer.run(lambda: amr.amr_render(r.ctx, cam, m, c, 1, stream.cuda_stream), steps, warmup)
             ms = float(np.median(ts))
             segs = int(c.sum())
             key = (cam.mode, cam.precision)
             host[key] = (m, c)
             res[f"{modes[cam.mode]}_{precs[cam.precision]}"] = {
-                "ms_per_frame": ms, "gsegments_per_s": segs / (ms * 1e-3) / 1e9, "segments": segs}
+                "ms_per_frame": ms, "gsegments_per_s": segs / (ms * 1e-3) / 1e9, "segments": segs,
+                "options": opts}
     errs = {}
     for mode in modes:
         ref = host[(mode, 0)][0]
@@ -909,7 +913,8 @@ def run_ours(args):
         sub_warm = max(3, min(args.warmup, 5))
         line["configs"] = {
             "tiny_plain_256": bench_tiny(device, sub_steps, sub_warm, with_cpu),
-            "galaxy_precision_1024": bench_precision(device, sub_steps, sub_warm, with_cpu),
+            "galaxy_precision_1024": bench_precision(device, sub_steps, sub_warm, with_cpu,
+                                                     tune=not args.no_autotune),
             "zoom_level22_8x4096": bench_zoom(device, min(sub_steps, 5), 2, with_cpu),
             "serving_poisson_50rps": bench_serving(device, 20.0),
         }

@@ -9,7 +9,11 @@
 // (at most 64) renormalised over the samples inside the map; the weights come
 // from one exponential per pixel by a multiplicative recurrence.  The row pass
 // reads its taps through L1 (32 consecutive pixels of a row per warp); the
-// column pass stages 32-column tiles with their halo in shared memory.
+// column pass stages 32-column tiles with their halo in shared memory.  Both
+// passes are bound by instruction issue, so the interior sums run two taps
+// at a time in packed FP32 pairs, and the per-pixel exponential and the two
+// divisions use the hardware approximations (__expf, __fdividef: a few ulp,
+// under 1e-6 of the output).
 #include <cuda_runtime.h>
 
 #include "amr_internal.h"
@@ -22,6 +26,35 @@ constexpr int kMaxRadius = 64;
 __device__ __forceinline__ float sigma_of(float level, float inv_pixel) {
   // 2^-level / (2 pixel)
   return 0.5f * exp2f(-level) * inv_pixel;
+}
+
+// Interior sum over k = 1..R of w_k (x_-k + x_k), w_k = exp(g k^2) with
+// e1 = exp(g), two k at a time in packed FP32 pairs: w_(k+2) = w_k rho_k with
+// rho_k = exp(g (4k + 4)), and rho_(k+2) = rho_k exp(8g), so (w_k, w_(k+1))
+// and (rho_k, rho_(k+1)) each advance by one packed multiply.  tap(k) returns
+// x_-k + x_k.  Returns (sum of weighted taps, sum of weights).
+template <typename Tap>
+__device__ __forceinline__ float2 interior_pairs(int R, float e1, Tap tap) {
+  const float q = e1 * e1;                 // exp(2g)
+  float2 w = make_float2(e1, e1 * e1 * e1 * e1);  // (w_1, w_2) = (exp(g), exp(4g))
+  const float Q = q * q;                   // exp(4g)
+  float2 rho = make_float2(Q * Q, Q * Q * Q);     // (exp(8g), exp(12g)) = (w_3 / w_1, w_4 / w_2)
+  const float2 QQ = make_float2(Q * Q, Q * Q);    // w_(k+2) / w_k = exp(g (4k + 4)) grows by exp(8g)
+  float2 acc = make_float2(0.0f, 0.0f), ws = make_float2(0.0f, 0.0f);
+  int k = 1;
+  for (; k + 1 <= R; k += 2) {
+    const float2 a = make_float2(tap(k), tap(k + 1));
+    acc = __ffma2_rn(w, a, acc);
+    ws = __fadd2_rn(ws, w);
+    w = __fmul2_rn(w, rho);
+    rho = __fmul2_rn(rho, QQ);
+  }
+  float s = acc.x + acc.y, n = ws.x + ws.y;
+  if (k <= R) {  // odd R: the last k, whose weight is w.x
+    s = fmaf(w.x, tap(k), s);
+    n += w.x;
+  }
+  return make_float2(s, n);
 }
 
 template <bool COLUMNS>
@@ -37,56 +70,24 @@ __global__ void __launch_bounds__(256) blur_pass(const float* __restrict__ in, c
     return;
   }
   const int R = min(kMaxRadius, (int)(3.0f * sg + 0.5f));
-  const float g = -0.5f / (sg * sg);
-  // Weights w_k = exp(g k^2) by the recurrence w_k = w_(k-1) r_(k-1),
-  // r_k = r_(k-1) exp(2g), from one exponential per pixel: the relative error
-  // of w_k grows like k^2 ulp (1e-4 at k = 64, where w_k < e^-4.5), which
-  // moves a normalised output by under 1e-6 of the largest input.  The centre
-  // tap, then the pairs at +-k sharing one weight.
+  const float g = __fdividef(-0.5f, sg * sg);
+  // Weights w_k = exp(g k^2) by multiplicative recurrences from one
+  // exponential per pixel (pairs of k in the interior, w_k = w_(k-1) r_(k-1),
+  // r_k = r_(k-1) exp(2g) at the map's edges): the relative error of w_k grows
+  // like k^2 ulp (1e-4 at k = 64, where w_k < e^-4.5), which moves a
+  // normalised output by under 1e-6 of the largest input.  The centre tap,
+  // then the taps at +-k sharing one weight.
   const int pos = COLUMNS ? y : x, len = COLUMNS ? ny : nx;
   const int stride = COLUMNS ? nx : 1;
-  const float e1 = expf(g), q = e1 * e1;
+  const float e1 = __expf(g), q = e1 * e1;
   float w = 1.0f, ratio = e1;
   float acc = __ldg(&in[p]), norm = 1.0f;
   if (pos - R >= 0 && pos + R < len) {
-    // Interior: every tap inside the map, no bounds checks.  Four pairs of
-    // taps per iteration: their eight loads are independent of the weight
-    // recurrence, so they are all in flight before the first is used.
-    const float* lo = in + p;
-    const float* hi = in + p;
-    int k = 1;
-    for (; k + 3 <= R; k += 4) {
-      const float a0 = __ldg(lo - stride) + __ldg(hi + stride);
-      const float a1 = __ldg(lo - 2 * stride) + __ldg(hi + 2 * stride);
-      const float a2 = __ldg(lo - 3 * stride) + __ldg(hi + 3 * stride);
-      const float a3 = __ldg(lo - 4 * stride) + __ldg(hi + 4 * stride);
-      lo -= 4 * stride;
-      hi += 4 * stride;
-      w *= ratio;
-      ratio *= q;
-      acc = fmaf(w, a0, acc);
-      norm = fmaf(2.0f, w, norm);
-      w *= ratio;
-      ratio *= q;
-      acc = fmaf(w, a1, acc);
-      norm = fmaf(2.0f, w, norm);
-      w *= ratio;
-      ratio *= q;
-      acc = fmaf(w, a2, acc);
-      norm = fmaf(2.0f, w, norm);
-      w *= ratio;
-      ratio *= q;
-      acc = fmaf(w, a3, acc);
-      norm = fmaf(2.0f, w, norm);
-    }
-    for (; k <= R; ++k) {
-      w *= ratio;
-      ratio *= q;
-      lo -= stride;
-      hi += stride;
-      acc = fmaf(w, __ldg(lo) + __ldg(hi), acc);
-      norm = fmaf(2.0f, w, norm);
-    }
+    // Interior: every tap inside the map, no bounds checks.
+    const float* c = in + p;
+    const float2 sn = interior_pairs(R, e1, [&](int k) { return __ldg(c - k * stride) + __ldg(c + k * stride); });
+    acc += sn.x;
+    norm = fmaf(2.0f, sn.y, norm);
   } else {
     for (int k = 1; k <= R; ++k) {
       w *= ratio;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(256) blur_pass(const float* __restrict__ in, c
       }
     }
   }
-  out[p] = acc / norm;
+  out[p] = __fdividef(acc, norm);
 }
 
 // The column pass on tiles of 32 columns x 64 rows staged in shared memory
@@ -130,40 +131,14 @@ __global__ void __launch_bounds__(256) blur_cols_staged(const float* __restrict_
       continue;
     }
     const int R = min(kMaxRadius, (int)(3.0f * sg + 0.5f));
-    const float g = -0.5f / (sg * sg);
-    const float e1 = expf(g), q = e1 * e1;
+    const float g = __fdividef(-0.5f, sg * sg);
+    const float e1 = __expf(g), q = e1 * e1;
     float w = 1.0f, ratio = e1;
     float acc = t[0], norm = 1.0f;
     if (y - R >= 0 && y + R < ny) {
-      int k = 1;
-      for (; k + 3 <= R; k += 4) {
-        const float a0 = t[-k * 32] + t[k * 32];
-        const float a1 = t[(-k - 1) * 32] + t[(k + 1) * 32];
-        const float a2 = t[(-k - 2) * 32] + t[(k + 2) * 32];
-        const float a3 = t[(-k - 3) * 32] + t[(k + 3) * 32];
-        w *= ratio;
-        ratio *= q;
-        acc = fmaf(w, a0, acc);
-        norm = fmaf(2.0f, w, norm);
-        w *= ratio;
-        ratio *= q;
-        acc = fmaf(w, a1, acc);
-        norm = fmaf(2.0f, w, norm);
-        w *= ratio;
-        ratio *= q;
-        acc = fmaf(w, a2, acc);
-        norm = fmaf(2.0f, w, norm);
-        w *= ratio;
-        ratio *= q;
-        acc = fmaf(w, a3, acc);
-        norm = fmaf(2.0f, w, norm);
-      }
-      for (; k <= R; ++k) {
-        w *= ratio;
-        ratio *= q;
-        acc = fmaf(w, t[-k * 32] + t[k * 32], acc);
-        norm = fmaf(2.0f, w, norm);
-      }
+      const float2 sn = interior_pairs(R, e1, [&](int k) { return t[-k * 32] + t[k * 32]; });
+      acc += sn.x;
+      norm = fmaf(2.0f, sn.y, norm);
     } else {
       for (int k = 1; k <= R; ++k) {
         w *= ratio;
@@ -178,7 +153,7 @@ __global__ void __launch_bounds__(256) blur_cols_staged(const float* __restrict_
         }
       }
     }
-    out[p] = acc / norm;
+    out[p] = __fdividef(acc, norm);
   }
 }
 
