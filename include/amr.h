@@ -316,10 +316,14 @@ amr_status amr_render_batch_partial(amr_ctx* ctx, int32_t n, const amr_camera* c
 amr_status amr_merge_partials(int32_t n_parts, int32_t mode, int32_t precision, int64_t n_px,
                               const void* const* partials, void* map_out, void* cuda_stream);
 
-/* JSON counters: renders, rays, segments, tree bytes, options, server latency. */
+/* JSON counters: renders, rays, segments, tree bytes (and the packed
+ * weighted-mean copies), options, registers per thread of the batch kernels at
+ * the current cap, server latency. */
 amr_status amr_stats(amr_ctx* ctx, char* json_buf, int64_t buf_len);
 
-/* Device memory the loaded tree occupies, its oct count and depth. */
+/* Device memory the loaded tree occupies (records, link blocks, fields; the
+ * packed weighted-mean copies are counted in amr_stats), its oct count and
+ * depth. */
 amr_status amr_tree_info(amr_ctx* ctx, int64_t* n_oct, int32_t* depth, int64_t* device_bytes);
 
 /* Message of the calling thread's last error (static storage; ctx may be NULL). */
