@@ -830,11 +830,12 @@ void admit_locked(amr_ctx* ctx) {
     std::shared_ptr<Request> r = ctx->queue.front();
     if (ctx->srv_used + r->bytes > ctx->srv_budget && ctx->srv_used > 0) return;
     CamDev d;
-    if (canonicalise(ctx, r->cam, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h, d) != AMR_OK ||
-        attach_pack(ctx, r->cam, d) != AMR_OK) {
+    amr_status cst = canonicalise(ctx, r->cam, ctx->srv_opt.tile_w, ctx->srv_opt.tile_h, d);
+    if (cst == AMR_OK) cst = attach_pack(ctx, r->cam, d);
+    if (cst != AMR_OK) {
       ctx->queue.pop_front();
       ctx->srv_used += r->bytes;
-      finish_locked(ctx, r, AMR_E_INVALID, g_err);
+      finish_locked(ctx, r, cst, g_err);
       ctx->done_cv.notify_all();
       continue;
     }
