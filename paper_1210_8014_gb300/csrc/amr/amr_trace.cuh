@@ -252,11 +252,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   // changes or a step crosses an edge or a corner.  A local copy is read back
   // there, so they are not live (in registers) across the common step.
   volatile long long keepX[3];
-  volatile int keepD[3];
+  volatile int keepD[3], keepA[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     keepX[a] = X[a];
     keepD[a] = D[a];
+    keepA[a] = aD[a];
   }
   auto reload = [&]() {
 #pragma unroll
@@ -269,6 +270,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     s1 = D[1] > 0 ? 1 : -1;
     s2 = D[2] > 0 ? 1 : -1;
     L = cam.L;
+  };
+  // The one-level coarsening needs only |D|.
+  auto reload_aD = [&]() {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) aD[a] = keepA[a];
   };
 
   // ---- accumulators ---------------------------------------------------------
@@ -393,11 +399,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         o = (uint32_t)v;
         continue;
       }
-      reload();
       if ((uint32_t)v < A.n_oct) {
+        reload();
         r.y = ry;
         o = (uint32_t)v;
       } else if (v == kCornerLink) {
+        reload();
         // Several axes at once, leaving the oct (an edge or corner): from the root.
         c ^= stepbits;  // back to the cell the ray leaves
         load_k();
@@ -431,6 +438,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         lvl = (int)((r.y >> 8) & 31u);
         if (lvl < 1 || lvl >= lvl0) { bad = true; break; }
         if (lvl == lvl0 - 1) {
+          reload_aD();
           // One level up, the common case: the coarser leaf is the parent of
           // the cell the step entered, so on each axis its exit plane is that
           // cell's, or one cell of the old size s farther when the cell lies in
@@ -462,10 +470,12 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
             sf = __fmul_rn(sf, 2.0f);
           }
         } else {
+          reload();
           load_k();
           recompute();
         }
         lmask = 0xFFu;  // coarser than before, so above the cut
+        continue;       // the coarser leaf is unrefined: nothing to enter
       }
       if (((r.y >> c) & 1u) && lvl < L) {
         // The neighbour is refined: enter its child oct, go on down by mid-planes.
