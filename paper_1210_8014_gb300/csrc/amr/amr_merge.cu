@@ -11,7 +11,8 @@
 // s + t = a + b exactly), carries every rounding error and low part in a
 // second accumulator, and only then divides the weighted mean.  One thread per
 // pixel; all reads are coalesced and each partial is read once, so the merge
-// is bound by HBM bandwidth.
+// is bound by HBM bandwidth, provided each thread keeps several reads in
+// flight: the FP32 paths issue four domains' loads before adding them.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -71,13 +72,35 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeArgs a) {
       for (int d = 0; d < a.n_parts; ++d) v = fmax(v, __ldg(static_cast<const T*>(a.parts[d]) + p));
     } else if (sizeof(T) == 4) {
       // FP32 partials: column (s, c) float2; weighted (S, cS, N, cN) float4.
+      // Four domains' loads are issued before their sums, so each thread has
+      // four reads in flight (the additions keep the domain order).
       CSum<float> S, N;
-      for (int d = 0; d < a.n_parts; ++d) {
-        if (weighted) {
+      int d = 0;
+      if (weighted) {
+        for (; d + 4 <= a.n_parts; d += 4) {
+          float4 q[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) q[u] = __ldg(static_cast<const float4*>(a.parts[d + u]) + p);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            S.add(q[u].x, q[u].y);
+            N.add(q[u].z, q[u].w);
+          }
+        }
+        for (; d < a.n_parts; ++d) {
           const float4 q = __ldg(static_cast<const float4*>(a.parts[d]) + p);
           S.add(q.x, q.y);
           N.add(q.z, q.w);
-        } else {
+        }
+      } else {
+        for (; d + 4 <= a.n_parts; d += 4) {
+          float2 q[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) q[u] = __ldg(static_cast<const float2*>(a.parts[d + u]) + p);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) S.add(q[u].x, q[u].y);
+        }
+        for (; d < a.n_parts; ++d) {
           const float2 q = __ldg(static_cast<const float2*>(a.parts[d]) + p);
           S.add(q.x, q.y);
         }
