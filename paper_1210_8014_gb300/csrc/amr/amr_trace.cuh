@@ -251,7 +251,8 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   uint32_t lmask = lvl < L ? 0xFFu : 0u;
   // The ray's origin and direction are needed again only where the level
   // changes or a step crosses an edge or a corner.  A local copy is read back
-  // there, so they are not live (in registers) across the common step.
+  // there, so they are not live (in registers) across the common step; the
+  // one-level coarsening reads back |D| alone.
   volatile long long keepX[3];
   volatile int keepD[3], keepA[3];
 #pragma unroll
@@ -429,7 +430,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       } else {
         if (v == -1) break;
         if (v >= 0) { bad = true; break; }
-        // A coarser leaf: an unrefined cell, so the test below skips it.
+        // A coarser leaf: an unrefined cell, so nothing to enter after it.
         const int cr = -v - 2;
         if (((uint32_t)cr >> 3) >= A.n_oct) { bad = true; break; }
         const int cv = c;  // the same-level cell the step entered (no oct of that level exists there)
