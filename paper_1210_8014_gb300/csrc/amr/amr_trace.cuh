@@ -220,6 +220,10 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   // and 0 at index 6; a small per-thread array read with one indexed load per step.
   float restv[7];
   restv[6] = 0.0f;
+  // The remainders r01, r02, r12 of the current level as exact 32-bit
+  // integers (exact from level 4 down, where s <= 2^32), kept in local memory
+  // for the incremental descent of the FP32 kernels with links.
+  volatile uint32_t rex[3];
   float sf = 0.0f;                                      // s as a float
   auto recompute = [&]() {
     const int sh = kFixBits - lvl;
@@ -237,6 +241,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     F01 = 2 * (int)E01 + (r01 != 0);
     F02 = 2 * (int)E02 + (r02 != 0);
     F12 = 2 * (int)E12 + (r12 != 0);
+    if (NB && PREC != AMR_PREC_FP64) {
+      rex[0] = (uint32_t)r01;
+      rex[1] = (uint32_t)r02;
+      rex[2] = (uint32_t)r12;
+    }
     const long long s = 1LL << sh;
     restv[0] = __ll2float_rn(r01); restv[1] = __ll2float_rn(s - r01);
     restv[2] = __ll2float_rn(r02); restv[3] = __ll2float_rn(s - r02);
@@ -479,6 +488,13 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
               if (G12 & 1) restv[4] = __fadd_rn(restv[4], sf); else restv[5] = __fadd_rn(restv[5], sf);
             }
             sf = __fmul_rn(sf, 2.0f);
+            // The exact remainders gain s where the dropped bit is 1 (only
+            // used from level 4 down, where they fit 32 bits).
+            const int sho = kFixBits - lvl0;
+            const uint32_t add = sho < 32 ? (1u << sho) : 0u;
+            rex[0] = rex[0] + ((G01 & 1) ? add : 0u);
+            rex[1] = rex[1] + ((G02 & 1) ? add : 0u);
+            rex[2] = rex[2] + ((G12 & 1) ? add : 0u);
           }
         } else {
           reload();
@@ -489,20 +505,78 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         continue;       // the coarser leaf is unrefined: nothing to enter
       }
       if (((r.y >> c) & 1u) && lvl < L) {
-        // The neighbour is refined: enter its child oct, go on down by mid-planes.
-        load_k();
-        const int sh = kFixBits - lvl;
-        const int ka = sel3(ea, k0, k1, k2);
-        const long long Xa = sel3(ea, X[0], X[1], X[2]);
-        m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
-        dA = sel3(ea, aD[0], aD[1], aD[2]);
-        const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
-        if (ch >= A.n_oct) { bad = true; break; }
-        o = ch;
-        r = __ldg(&rec[o]);
-        descend(lvl + 1, lvl, k0, k1, k2);
-        if (bad) break;
-        recompute();
+        // The neighbour is refined: enter its child oct, go on down.
+        if (PREC != AMR_PREC_FP64 && lvl >= 4 && aD[0] != 0 && aD[1] != 0 && aD[2] != 0) {
+          // Exact incremental descent.  The ray entered this cell through
+          // its face on axis ea, so on ea the child is the half next to that
+          // face.  On another axis a, with the pair term e = H s' + r' in
+          // units of the child size s' (H = 2E + the top bit of r, r' its
+          // low bits), the entry point lies in the half the ray reaches
+          // first iff the entry time precedes the mid-plane crossing:
+          // e_(ea,a) < (2|D_a| - |D_ea|) s', i.e. H < T when ea < a and
+          // 2(H + T) + [r' > 0] > 0 when ea > a (e_(ea,a) = -e there).  The
+          // child's exit planes are the mid-planes on the first-reached
+          // axes: E' = H - (u_x |D_y| - u_y |D_x|), r' the low bits.
+          uint32_t R0 = rex[0], R1 = rex[1], R2 = rex[2];
+          do {
+            const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+            if (ch >= A.n_oct) { bad = true; break; }
+            o = ch;
+            r = __ldg(&rec[o]);
+            const int shc = kFixBits - lvl - 1;  // <= 31 from level 4 down
+            const int t0 = (int)((R0 >> shc) & 1u), t1 = (int)((R1 >> shc) & 1u), t2 = (int)((R2 >> shc) & 1u);
+            const uint32_t low = (1u << shc) - 1u;
+            R0 &= low;
+            R1 &= low;
+            R2 &= low;
+            const int H0 = (F01 & ~1) | t0, H1 = (F02 & ~1) | t1, H2 = (F12 & ~1) | t2;
+            int u0, u1, u2;
+            if (ea == 0) {
+              u0 = 1;
+              u1 = H0 < 2 * aD[1] - aD[0];
+              u2 = H1 < 2 * aD[2] - aD[0];
+            } else if (ea == 1) {
+              u1 = 1;
+              u0 = 2 * (H0 + 2 * aD[0] - aD[1]) + (R0 != 0u) > 0;
+              u2 = H2 < 2 * aD[2] - aD[1];
+            } else {
+              u2 = 1;
+              u0 = 2 * (H1 + 2 * aD[0] - aD[2]) + (R1 != 0u) > 0;
+              u1 = 2 * (H2 + 2 * aD[1] - aD[2]) + (R2 != 0u) > 0;
+            }
+            F01 = 2 * (H0 - (u0 * aD[1] - u1 * aD[0])) + (R0 != 0u);
+            F02 = 2 * (H1 - (u0 * aD[2] - u2 * aD[0])) + (R1 != 0u);
+            F12 = 2 * (H2 - (u1 * aD[2] - u2 * aD[1])) + (R2 != 0u);
+            // The first-reached half is the low child when the ray moves up
+            // that axis, the high one when it moves down.
+            c = dirbits ^ (~(u0 | (u1 << 1) | (u2 << 2)) & 7);
+            ++lvl;
+          } while (((r.y >> c) & 1u) && lvl < L);
+          if (bad) break;
+          rex[0] = R0;
+          rex[1] = R1;
+          rex[2] = R2;
+          const uint32_t sN = 1u << (kFixBits - lvl);
+          restv[0] = __uint2float_rn(R0); restv[1] = __uint2float_rn(sN - R0);
+          restv[2] = __uint2float_rn(R1); restv[3] = __uint2float_rn(sN - R1);
+          restv[4] = __uint2float_rn(R2); restv[5] = __uint2float_rn(sN - R2);
+          sf = __int_as_float((127 + kFixBits - lvl) << 23);
+        } else {
+          // By mid-planes from the cell's coordinates, then the 64-bit terms.
+          load_k();
+          const int sh = kFixBits - lvl;
+          const int ka = sel3(ea, k0, k1, k2);
+          const long long Xa = sel3(ea, X[0], X[1], X[2]);
+          m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+          dA = sel3(ea, aD[0], aD[1], aD[2]);
+          const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+          if (ch >= A.n_oct) { bad = true; break; }
+          o = ch;
+          r = __ldg(&rec[o]);
+          descend(lvl + 1, lvl, k0, k1, k2);
+          if (bad) break;
+          recompute();
+        }
         lmask = lvl < L ? 0xFFu : 0u;
       }
     } else {
