@@ -411,9 +411,74 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
         continue;
       }
       if ((uint32_t)v < A.n_oct) {
-        reload();
+        // A valid link failed the common test: the neighbour is refined
+        // above the cut (lmask is 0xFF exactly while lvl < L).
         r.y = ry;
         o = (uint32_t)v;
+        if (PREC != AMR_PREC_FP64) {
+          // The exact incremental descent needs only |D| and the cut.
+          reload_aD();
+          if (lvl >= 4 && aD[0] != 0 && aD[1] != 0 && aD[2] != 0) {
+            L = cam.L;
+            // Exact incremental descent.  The ray entered this cell through
+            // its face on axis ea, so on ea the child is the half next to that
+            // face.  On another axis a, with the pair term e = H s' + r' in
+            // units of the child size s' (H = 2E + the top bit of r, r' its
+            // low bits), the entry point lies in the half the ray reaches
+            // first iff the entry time precedes the mid-plane crossing:
+            // e_(ea,a) < (2|D_a| - |D_ea|) s', i.e. H < T when ea < a and
+            // 2(H + T) + [r' > 0] > 0 when ea > a (e_(ea,a) = -e there).  The
+            // child's exit planes are the mid-planes on the first-reached
+            // axes: E' = H - (u_x |D_y| - u_y |D_x|), r' the low bits.
+            uint32_t R0 = rex[0], R1 = rex[1], R2 = rex[2];
+            do {
+              const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+              if (ch >= A.n_oct) { bad = true; break; }
+              o = ch;
+              r = __ldg(&rec[o]);
+              const int shc = kFixBits - lvl - 1;  // <= 31 from level 4 down
+              const int t0 = (int)((R0 >> shc) & 1u), t1 = (int)((R1 >> shc) & 1u), t2 = (int)((R2 >> shc) & 1u);
+              const uint32_t low = (1u << shc) - 1u;
+              R0 &= low;
+              R1 &= low;
+              R2 &= low;
+              const int H0 = (F01 & ~1) | t0, H1 = (F02 & ~1) | t1, H2 = (F12 & ~1) | t2;
+              int u0, u1, u2;
+              if (ea == 0) {
+                u0 = 1;
+                u1 = H0 < 2 * aD[1] - aD[0];
+                u2 = H1 < 2 * aD[2] - aD[0];
+              } else if (ea == 1) {
+                u1 = 1;
+                u0 = 2 * (H0 + 2 * aD[0] - aD[1]) + (R0 != 0u) > 0;
+                u2 = H2 < 2 * aD[2] - aD[1];
+              } else {
+                u2 = 1;
+                u0 = 2 * (H1 + 2 * aD[0] - aD[2]) + (R1 != 0u) > 0;
+                u1 = 2 * (H2 + 2 * aD[1] - aD[2]) + (R2 != 0u) > 0;
+              }
+              F01 = 2 * (H0 - (u0 * aD[1] - u1 * aD[0])) + (R0 != 0u);
+              F02 = 2 * (H1 - (u0 * aD[2] - u2 * aD[0])) + (R1 != 0u);
+              F12 = 2 * (H2 - (u1 * aD[2] - u2 * aD[1])) + (R2 != 0u);
+              // The first-reached half is the low child when the ray moves up
+              // that axis, the high one when it moves down.
+              c = dirbits ^ (~(u0 | (u1 << 1) | (u2 << 2)) & 7);
+              ++lvl;
+            } while (((r.y >> c) & 1u) && lvl < L);
+            if (bad) break;
+            rex[0] = R0;
+            rex[1] = R1;
+            rex[2] = R2;
+            const uint32_t sN = 1u << (kFixBits - lvl);
+            restv[0] = __uint2float_rn(R0); restv[1] = __uint2float_rn(sN - R0);
+            restv[2] = __uint2float_rn(R1); restv[3] = __uint2float_rn(sN - R1);
+            restv[4] = __uint2float_rn(R2); restv[5] = __uint2float_rn(sN - R2);
+            sf = __int_as_float((127 + kFixBits - lvl) << 23);
+            lmask = lvl < L ? 0xFFu : 0u;
+            continue;
+          }
+        }
+        reload();
       } else if (v == kCornerLink) {
         reload();
         // Several axes at once, leaving the oct (an edge or corner): from the root.
@@ -506,77 +571,20 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
       }
       if (((r.y >> c) & 1u) && lvl < L) {
         // The neighbour is refined: enter its child oct, go on down.
-        if (PREC != AMR_PREC_FP64 && lvl >= 4 && aD[0] != 0 && aD[1] != 0 && aD[2] != 0) {
-          // Exact incremental descent.  The ray entered this cell through
-          // its face on axis ea, so on ea the child is the half next to that
-          // face.  On another axis a, with the pair term e = H s' + r' in
-          // units of the child size s' (H = 2E + the top bit of r, r' its
-          // low bits), the entry point lies in the half the ray reaches
-          // first iff the entry time precedes the mid-plane crossing:
-          // e_(ea,a) < (2|D_a| - |D_ea|) s', i.e. H < T when ea < a and
-          // 2(H + T) + [r' > 0] > 0 when ea > a (e_(ea,a) = -e there).  The
-          // child's exit planes are the mid-planes on the first-reached
-          // axes: E' = H - (u_x |D_y| - u_y |D_x|), r' the low bits.
-          uint32_t R0 = rex[0], R1 = rex[1], R2 = rex[2];
-          do {
-            const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
-            if (ch >= A.n_oct) { bad = true; break; }
-            o = ch;
-            r = __ldg(&rec[o]);
-            const int shc = kFixBits - lvl - 1;  // <= 31 from level 4 down
-            const int t0 = (int)((R0 >> shc) & 1u), t1 = (int)((R1 >> shc) & 1u), t2 = (int)((R2 >> shc) & 1u);
-            const uint32_t low = (1u << shc) - 1u;
-            R0 &= low;
-            R1 &= low;
-            R2 &= low;
-            const int H0 = (F01 & ~1) | t0, H1 = (F02 & ~1) | t1, H2 = (F12 & ~1) | t2;
-            int u0, u1, u2;
-            if (ea == 0) {
-              u0 = 1;
-              u1 = H0 < 2 * aD[1] - aD[0];
-              u2 = H1 < 2 * aD[2] - aD[0];
-            } else if (ea == 1) {
-              u1 = 1;
-              u0 = 2 * (H0 + 2 * aD[0] - aD[1]) + (R0 != 0u) > 0;
-              u2 = H2 < 2 * aD[2] - aD[1];
-            } else {
-              u2 = 1;
-              u0 = 2 * (H1 + 2 * aD[0] - aD[2]) + (R1 != 0u) > 0;
-              u1 = 2 * (H2 + 2 * aD[1] - aD[2]) + (R2 != 0u) > 0;
-            }
-            F01 = 2 * (H0 - (u0 * aD[1] - u1 * aD[0])) + (R0 != 0u);
-            F02 = 2 * (H1 - (u0 * aD[2] - u2 * aD[0])) + (R1 != 0u);
-            F12 = 2 * (H2 - (u1 * aD[2] - u2 * aD[1])) + (R2 != 0u);
-            // The first-reached half is the low child when the ray moves up
-            // that axis, the high one when it moves down.
-            c = dirbits ^ (~(u0 | (u1 << 1) | (u2 << 2)) & 7);
-            ++lvl;
-          } while (((r.y >> c) & 1u) && lvl < L);
-          if (bad) break;
-          rex[0] = R0;
-          rex[1] = R1;
-          rex[2] = R2;
-          const uint32_t sN = 1u << (kFixBits - lvl);
-          restv[0] = __uint2float_rn(R0); restv[1] = __uint2float_rn(sN - R0);
-          restv[2] = __uint2float_rn(R1); restv[3] = __uint2float_rn(sN - R1);
-          restv[4] = __uint2float_rn(R2); restv[5] = __uint2float_rn(sN - R2);
-          sf = __int_as_float((127 + kFixBits - lvl) << 23);
-        } else {
-          // By mid-planes from the cell's coordinates, then the 64-bit terms.
-          load_k();
-          const int sh = kFixBits - lvl;
-          const int ka = sel3(ea, k0, k1, k2);
-          const long long Xa = sel3(ea, X[0], X[1], X[2]);
-          m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
-          dA = sel3(ea, aD[0], aD[1], aD[2]);
-          const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
-          if (ch >= A.n_oct) { bad = true; break; }
-          o = ch;
-          r = __ldg(&rec[o]);
-          descend(lvl + 1, lvl, k0, k1, k2);
-          if (bad) break;
-          recompute();
-        }
+        // By mid-planes from the cell's coordinates, then the 64-bit terms.
+        load_k();
+        const int sh = kFixBits - lvl;
+        const int ka = sel3(ea, k0, k1, k2);
+        const long long Xa = sel3(ea, X[0], X[1], X[2]);
+        m = sel3(ea, s0, s1, s2) > 0 ? ((long long)ka << sh) - Xa : Xa - ((long long)(ka + 1) << sh);
+        dA = sel3(ea, aD[0], aD[1], aD[2]);
+        const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
+        if (ch >= A.n_oct) { bad = true; break; }
+        o = ch;
+        r = __ldg(&rec[o]);
+        descend(lvl + 1, lvl, k0, k1, k2);
+        if (bad) break;
+        recompute();
         lmask = lvl < L ? 0xFFu : 0u;
       }
     } else {
