@@ -218,12 +218,11 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
   long long r01 = 0, r02 = 0, r12 = 0;                  // remainders (FP64 chords)
   // r and s - r of each pair as floats (FP32 chords), at 2 * pair + (ea < b),
   // and 0 at index 6; a small per-thread array read with one indexed load per step.
-  float restv[7];
+  // Entries 8..10 hold the remainders r01, r02, r12 of the current level as
+  // exact 32-bit integers (bit patterns; exact from level 4 down, where
+  // s <= 2^32) for the incremental descent of the FP32 kernels with links.
+  __align__(16) float restv[12];
   restv[6] = 0.0f;
-  // The remainders r01, r02, r12 of the current level as exact 32-bit
-  // integers (exact from level 4 down, where s <= 2^32), kept in local memory
-  // for the incremental descent of the FP32 kernels with links.
-  volatile uint32_t rex[3];
   float sf = 0.0f;                                      // s as a float
   auto recompute = [&]() {
     const int sh = kFixBits - lvl;
@@ -242,9 +241,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
     F02 = 2 * (int)E02 + (r02 != 0);
     F12 = 2 * (int)E12 + (r12 != 0);
     if (NB && PREC != AMR_PREC_FP64) {
-      rex[0] = (uint32_t)r01;
-      rex[1] = (uint32_t)r02;
-      rex[2] = (uint32_t)r12;
+      restv[8] = __uint_as_float((uint32_t)r01);
+      restv[9] = __uint_as_float((uint32_t)r02);
+      restv[10] = __uint_as_float((uint32_t)r12);
     }
     const long long s = 1LL << sh;
     restv[0] = __ll2float_rn(r01); restv[1] = __ll2float_rn(s - r01);
@@ -430,7 +429,7 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
             // 2(H + T) + [r' > 0] > 0 when ea > a (e_(ea,a) = -e there).  The
             // child's exit planes are the mid-planes on the first-reached
             // axes: E' = H - (u_x |D_y| - u_y |D_x|), r' the low bits.
-            uint32_t R0 = rex[0], R1 = rex[1], R2 = rex[2];
+            uint32_t R0 = __float_as_uint(restv[8]), R1 = __float_as_uint(restv[9]), R2 = __float_as_uint(restv[10]);
             do {
               const uint32_t ch = __ldg(&rec[o].x) + __popc(r.y & ((1u << c) - 1u));
               if (ch >= A.n_oct) { bad = true; break; }
@@ -466,9 +465,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
               ++lvl;
             } while (((r.y >> c) & 1u) && lvl < L);
             if (bad) break;
-            rex[0] = R0;
-            rex[1] = R1;
-            rex[2] = R2;
+            restv[8] = __uint_as_float(R0);
+            restv[9] = __uint_as_float(R1);
+            restv[10] = __uint_as_float(R2);
             const uint32_t sN = 1u << (kFixBits - lvl);
             restv[0] = __uint2float_rn(R0); restv[1] = __uint2float_rn(sN - R0);
             restv[2] = __uint2float_rn(R1); restv[3] = __uint2float_rn(sN - R1);
@@ -557,9 +556,9 @@ __device__ __forceinline__ RayOut trace_ray(const BatchArgs& A, const CamDev& ca
             // used from level 4 down, where they fit 32 bits).
             const int sho = kFixBits - lvl0;
             const uint32_t add = sho < 32 ? (1u << sho) : 0u;
-            rex[0] = rex[0] + ((G01 & 1) ? add : 0u);
-            rex[1] = rex[1] + ((G02 & 1) ? add : 0u);
-            rex[2] = rex[2] + ((G12 & 1) ? add : 0u);
+            restv[8] = __uint_as_float(__float_as_uint(restv[8]) + ((G01 & 1) ? add : 0u));
+            restv[9] = __uint_as_float(__float_as_uint(restv[9]) + ((G02 & 1) ? add : 0u));
+            restv[10] = __uint_as_float(__float_as_uint(restv[10]) + ((G12 & 1) ? add : 0u));
           }
         } else {
           reload();
